@@ -1,0 +1,246 @@
+/*
+ * halftime.h -- C ABI of libhalftime, a GB300 (sm_103a) implementation of
+ * HalftimeHash (J. Apple, "HalftimeHash: Modern Hashing without 64-bit
+ * Multipliers or Finite Fields", arXiv 2104.08865).
+ *
+ * The hash family maps a seed s and a byte string x to a 16, 24, 32 or
+ * 40-byte digest H(s, x) (Section 1, problem statement; Section 2, output
+ * widths).  Digests are k = width/8 little-endian 64-bit words.
+ *
+ * Conventions for every call:
+ *   - Return value: HT_OK (0) or a negative HT_ERR_* code.  ht_last_error()
+ *     gives a one-line description of the last error on the calling thread.
+ *   - The caller owns every data, length, pointer-array and digest buffer.
+ *     The library owns the opaque handles (ht_ctx, ht_server); release them
+ *     with the matching *_destroy call.
+ *   - "_dev" pointers are CUDA device pointers of the current device,
+ *     "_host" pointers are host pointers.  ht_stream_t is a cudaStream_t
+ *     (NULL = the legacy default stream).
+ *   - Calls that take a stream only enqueue work on it and return without
+ *     waiting; results are valid once the stream reaches that point.
+ *   - A context keeps per-call scratch state on the device, so calls on one
+ *     context must be ordered: issue them on one stream (or synchronise
+ *     between streams).  Use one context per concurrent stream.
+ *   - Lengths are bytes, 0 <= len < 2^64.
+ */
+#ifndef HALFTIME_H
+#define HALFTIME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ht_stream_t; /* same type as cudaStream_t */
+typedef struct ht_ctx ht_ctx;
+typedef struct ht_server ht_server;
+
+/* ---- status codes -------------------------------------------------------- */
+#define HT_OK 0
+#define HT_ERR_ARG -1      /* invalid argument (NULL pointer, size mismatch) */
+#define HT_ERR_WIDTH -2    /* width not in {16, 24, 32, 40} */
+#define HT_ERR_TOO_LONG -3 /* input or batch exceeds the context's capacity */
+#define HT_ERR_CUDA -4     /* a CUDA runtime call failed (message has detail) */
+#define HT_ERR_NOMEM -5    /* device or host allocation failed */
+#define HT_ERR_BUDGET -6   /* request larger than the server's memory budget */
+#define HT_ERR_TIMEOUT -7  /* a bounded wait ran out */
+#define HT_ERR_BUSY -8     /* server queue full / ticket not finished */
+#define HT_ERR_DEVICE -9   /* a kernel reported an error in the status word */
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to n bytes).  Returns the code of that error (HT_OK if none). */
+int ht_last_error(char *buf, size_t n);
+
+/* ---- seeds (Section 2 "input entropy"; Section 6.2 entropy budget) ----- */
+
+/* Number of 64-bit seed words a width consumes.  The words are laid out as
+ * E (e*w EHC hash keys), T (k*19*7 tree-node keys), F (k*19*8*8 final-NH
+ * keys) and R (8*d*w + k Toeplitz tail keys): the budget of Section 6.2 for
+ * 19 tree levels (enough for any length below 2^64), plus one tail key for
+ * the length word.  Widths 16/24/32/40 give 2865/4245/5598/6897 words.
+ * Returns 0 for an unsupported width. */
+size_t ht_seed_words(int width_bytes);
+
+/* Expands a 64-bit seed into the seed words of a width on the host: word i
+ * is the i-th output of splitmix64 (Steele, Lea, Flood, OOPSLA 2014) started
+ * at state seed64.  n_words must equal ht_seed_words(width_bytes).
+ * Errors: HT_ERR_WIDTH, HT_ERR_ARG (NULL out_words or wrong n_words). */
+int ht_seed_expand(uint64_t seed64, int width_bytes, uint64_t *out_words,
+                   size_t n_words);
+
+/* ---- context --------------------------------------------------------------
+ * A context binds one width to one seed on the current CUDA device: it
+ * uploads the seed words once, keeps the scratch memory of the tree stage
+ * (per-group node accumulators and completion counters, Section 5.2), the
+ * batch planner's buffers and the launch-shape cache of the autotuner.
+ * seed_words_host: n_words host words (n_words = ht_seed_words(width)).
+ * stream: the stream used for the uploads.
+ * Errors: HT_ERR_WIDTH, HT_ERR_ARG, HT_ERR_NOMEM, HT_ERR_CUDA. */
+int ht_ctx_create(int width_bytes, const uint64_t *seed_words_host,
+                  size_t n_words, ht_stream_t stream, ht_ctx **out);
+int ht_ctx_destroy(ht_ctx *ctx);
+
+/* Replaces the context's seed (same width): uploads the new words on
+ * `stream`; calls enqueued on that stream afterwards use them.  Errors:
+ * HT_ERR_ARG (wrong n_words), HT_ERR_CUDA. */
+int ht_ctx_rekey(ht_ctx *ctx, const uint64_t *seed_words_host, size_t n_words,
+                 ht_stream_t stream);
+
+/* Reserves device scratch so that ht_hash_batch can take up to max_strings
+ * strings whose lengths add up to at most max_total_bytes (the default after
+ * ht_ctx_create is 65536 strings and 64 GiB).  Synchronises the device.
+ * Errors: HT_ERR_ARG, HT_ERR_NOMEM, HT_ERR_CUDA. */
+int ht_ctx_reserve(ht_ctx *ctx, uint64_t max_total_bytes, size_t max_strings);
+
+/* Waits for `stream`, then reads and clears the context's device status
+ * word.  Returns HT_OK, or HT_ERR_TOO_LONG when a batch planned on the
+ * device exceeded the reserved scratch (that batch's digests were not
+ * written), or HT_ERR_CUDA. */
+int ht_ctx_status(ht_ctx *ctx, ht_stream_t stream);
+
+/* ---- hashing ----------------------------------------------------------------
+ * H(s, x) as in Section 5: generalized EHC over every 8*d*w-word execution
+ * (Section 3.3, Section 4, Section 5.1), k f-ary NH tree hashes over the EHC
+ * outputs with f = 8 (Section 3.1, Section 5.2, Eq. stack-construction), NH
+ * over the pending tree roots plus a Toeplitz-keyed NH over the unread tail
+ * and the length (Section 5.2, Section 6.1, Section 2). */
+
+/* Hashes one device-resident string.  data_dev: len bytes (any alignment;
+ * 16-byte aligned strings take the fast load path).  digest_dev: k words.
+ * Errors: HT_ERR_ARG, HT_ERR_NOMEM (scratch growth failed), HT_ERR_CUDA. */
+int ht_hash(ht_ctx *ctx, const void *data_dev, uint64_t len,
+            uint64_t *digest_dev, ht_stream_t stream);
+
+/* Hashes one string held in host memory (pinned memory gives full copy
+ * speed; pageable memory works but is slower).  The string is copied to the
+ * device in pieces on an internal copy stream while earlier pieces are
+ * hashed; digest_host (k words) is written before the call returns, so this
+ * call is synchronous.  Errors: as ht_hash, plus HT_ERR_NOMEM for the
+ * staging buffer. */
+int ht_hash_host(ht_ctx *ctx, const void *data_host, uint64_t len,
+                 uint64_t *digest_host, ht_stream_t stream);
+
+/* Hashes `count` device-resident strings in one persistent launch (the batch
+ * form): ptrs_dev[i] / lens_dev[i] (device arrays) describe string i, and
+ * digests_dev receives count*k words, string i at digests_dev + i*k.  A
+ * device planner turns the lengths into a (string, chunk) work list; warps
+ * take chunks from an atomic cursor; per-string completion counters finish
+ * each string's trees and run its finaliser inside the same kernel.  The
+ * planner and the kernel are replayed from a CUDA graph.  The batch must fit
+ * the scratch reserved by ht_ctx_reserve: the planner checks this on the
+ * device and, if it does not fit, writes no digests and records
+ * HT_ERR_TOO_LONG for ht_ctx_status (the host cannot see device lengths).
+ * Errors (host side): HT_ERR_ARG, HT_ERR_TOO_LONG (count above the reserve),
+ * HT_ERR_CUDA. */
+int ht_hash_batch(ht_ctx *ctx, const void *const *ptrs_dev,
+                  const uint64_t *lens_dev, size_t count, uint64_t *digests_dev,
+                  ht_stream_t stream);
+
+/* The one-launch-per-string comparator of ht_hash_batch: ptrs_host and
+ * lens_host are HOST arrays (of device pointers and lengths); string i is
+ * hashed by its own ht_hash launch into digests_dev + i*k.  Same digests.
+ * Errors: as ht_hash. */
+int ht_hash_batch_naive(ht_ctx *ctx, const void *const *ptrs_host,
+                        const uint64_t *lens_host, size_t count,
+                        uint64_t *digests_dev, ht_stream_t stream);
+
+/* ---- launch shapes and autotuning ------------------------------------------
+ * A launch shape is (chunk height L: a warp hashes 8^L executions before
+ * handing its tree root to the cross-warp levels; threads per block; blocks
+ * per SM).  The context caches one shape per length bucket
+ * (bucket = floor(log2(len)), 0..63) and one for batches. */
+typedef struct ht_shape {
+  int chunk_levels;      /* L: 2 or 3 */
+  int threads_per_block; /* 64 .. 1024, multiple of 32 */
+  int blocks_per_sm;     /* 1 .. 32; clamped to the occupancy limit */
+} ht_shape;
+
+/* Times every candidate shape on a device buffer of `len` bytes (allocated
+ * and freed inside the call) and stores the fastest in the bucket of len;
+ * writes it to *best if best is not NULL.  Synchronous.  Errors: HT_ERR_ARG,
+ * HT_ERR_NOMEM, HT_ERR_CUDA. */
+int ht_autotune(ht_ctx *ctx, uint64_t len, ht_stream_t stream, ht_shape *best);
+
+/* Reads / overrides the cached shape of the bucket of `len`
+ * (len = UINT64_MAX selects the batch shape).  Errors: HT_ERR_ARG. */
+int ht_get_shape(ht_ctx *ctx, uint64_t len, ht_shape *out);
+int ht_set_shape(ht_ctx *ctx, uint64_t len, const ht_shape *shape);
+
+/* Number of kernels this context has launched so far (planner and hash
+ * kernels; graph replays count their kernel nodes). */
+uint64_t ht_ctx_launches(ht_ctx *ctx);
+
+/* ---- serving: continuous batching -------------------------------------------
+ * A server admits hash requests as they arrive and keeps the GPU busy with
+ * overlapping batches: a dispatcher thread forms a batch of the requests
+ * that fit the free device memory (the budget) and a free stream slot,
+ * stages pinned-host requests into a device arena, launches the batch graph
+ * on that slot's stream and copies the digests back; a completion thread
+ * retires batches as their events fire, releases their memory and wakes
+ * waiters.  Seeds and in-flight tree state stay on the device.  Every
+ * request's arrival, launch and completion times are recorded (host
+ * steady clock) for latency percentiles. */
+typedef struct ht_server_opts {
+  int n_streams;          /* concurrent batches in flight (default 4) */
+  size_t max_batch;       /* requests per batch (default 4096) */
+  size_t max_queue;       /* queued requests before submit says BUSY (default 1<<20) */
+  uint64_t max_wait_us;   /* longest a request waits for batch-mates (default 0) */
+} ht_server_opts;
+
+typedef struct ht_server_stats_t {
+  uint64_t submitted, completed, rejected, batches;
+  uint64_t bytes_completed;
+  double p50_us, p99_us, mean_us, max_us; /* arrival -> digest ready, completed requests */
+  double wall_s;                          /* first arrival -> last completion */
+} ht_server_stats_t;
+
+/* Creates a server hashing with ctx's width and seed.  budget_bytes bounds
+ * the device memory the server holds for request data in flight (the arena
+ * is allocated here).  opts may be NULL for defaults.  The server owns its
+ * own contexts and streams; ctx only provides width and seed and may be
+ * destroyed afterwards.  Errors: HT_ERR_ARG, HT_ERR_NOMEM, HT_ERR_CUDA. */
+int ht_server_create(ht_ctx *ctx, uint64_t budget_bytes,
+                     const ht_server_opts *opts, ht_server **out);
+
+/* Submits one request: `ptr` is either a device pointer (ptr_is_host_pinned
+ * = 0; the data must stay valid until the request completes) or a host
+ * pointer to pinned memory (ptr_is_host_pinned = 1; copied into the arena).
+ * digest_host receives k words when the request completes.  *ticket
+ * identifies the request.  Errors: HT_ERR_ARG, HT_ERR_BUDGET (len above the
+ * budget: can never be admitted), HT_ERR_BUSY (queue full). */
+int ht_server_submit(ht_server *srv, const void *ptr, uint64_t len,
+                     int ptr_is_host_pinned, uint64_t *digest_host,
+                     uint64_t *ticket);
+
+/* *done = 1 once the request's digest is in digest_host.  Errors: HT_ERR_ARG
+ * (unknown ticket). */
+int ht_server_poll(ht_server *srv, uint64_t ticket, int *done);
+
+/* Blocks until the request completes or timeout_us passes (HT_ERR_TIMEOUT).
+ * A failed batch reports its error here (HT_ERR_CUDA / HT_ERR_DEVICE). */
+int ht_server_wait(ht_server *srv, uint64_t ticket, uint64_t timeout_us);
+
+/* Removes a request that is still queued (not yet launched); waiters on it
+ * then get HT_ERR_ARG.  Returns HT_OK, HT_ERR_BUSY when the request was
+ * already launched or finished, or HT_ERR_ARG (unknown ticket). */
+int ht_server_cancel(ht_server *srv, uint64_t ticket);
+
+/* Blocks until every submitted request has completed or timeout_us passes. */
+int ht_server_drain(ht_server *srv, uint64_t timeout_us);
+
+/* Statistics over completed requests since creation or the last reset. */
+int ht_server_stats(ht_server *srv, ht_server_stats_t *out, int reset);
+
+/* Per-request latencies (us, completion order) of completed requests since
+ * the last reset: writes up to n values, returns how many were written. */
+size_t ht_server_latencies(ht_server *srv, double *out_us, size_t n);
+
+int ht_server_destroy(ht_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HALFTIME_H */

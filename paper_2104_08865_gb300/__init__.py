@@ -1,0 +1,104 @@
+"""GB300 (sm_103a) HalftimeHash: the CUDA library libhalftime and its binding.
+
+``abi`` mirrors the C ABI of include/halftime.h name for name; ``Hasher`` is
+a convenience wrapper over one context that works with torch tensors for
+device memory and streams.  All hashing runs in the CUDA kernels.
+"""
+from __future__ import annotations
+
+import importlib
+
+import numpy as np
+
+__all__ = ["abi", "HalftimeError", "WIDTHS", "Hasher", "digest_words"]
+WIDTHS = (16, 24, 32, 40)
+
+
+def __getattr__(name):
+    # the binding loads libhalftime.so on first use and raises ImportError if
+    # the library has not been built (no fallback path exists)
+    if name == "abi":
+        return importlib.import_module(".abi", __name__)
+    if name == "HalftimeError":
+        return importlib.import_module(".abi", __name__).HalftimeError
+    raise AttributeError(name)
+
+
+def _abi():
+    return importlib.import_module(".abi", __name__)
+
+
+def digest_words(width: int) -> int:
+    return width // 8
+
+
+class Hasher:
+    """One context: a width and an expanded seed on the current device."""
+
+    def __init__(self, width: int, seed64: int = None, seed_words=None, stream=None):
+        if seed_words is None:
+            seed_words = _abi().ht_seed_expand(seed64 if seed64 is not None else 0, width)
+        self.width = width
+        self.k = width // 8
+        self.seed_words = np.ascontiguousarray(seed_words, dtype=np.uint64)
+        self.ctx = _abi().ht_ctx_create(width, self.seed_words, stream)
+
+    def close(self):
+        if self.ctx:
+            _abi().ht_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # device-resident inputs (torch tensors) --------------------------------
+    def hash(self, data, length: int = None, out=None, offset: int = 0, stream=None):
+        """Digest of a uint8 CUDA tensor (or a byte range of it) -> int64[k] tensor."""
+        import torch
+        n = data.numel() * data.element_size() - offset if length is None else length
+        if out is None:
+            out = torch.empty(self.k, dtype=torch.int64, device=data.device)
+        _abi().ht_hash(self.ctx, data.data_ptr() + offset, n, out.data_ptr(),
+                    stream if stream is not None else torch.cuda.current_stream())
+        return out
+
+    def hash_batch(self, ptrs_dev, lens_dev, count: int, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((count, self.k), dtype=torch.int64, device=ptrs_dev.device)
+        _abi().ht_hash_batch(self.ctx, ptrs_dev.data_ptr(), lens_dev.data_ptr(), count,
+                          out.data_ptr(), stream if stream is not None else torch.cuda.current_stream())
+        return out
+
+    def hash_batch_naive(self, ptrs_host, lens_host, out, stream=None):
+        import torch
+        ptrs_host = np.ascontiguousarray(ptrs_host, dtype=np.uint64)
+        lens_host = np.ascontiguousarray(lens_host, dtype=np.uint64)
+        _abi().ht_hash_batch_naive(self.ctx, ptrs_host, lens_host, len(lens_host), out.data_ptr(),
+                                stream if stream is not None else torch.cuda.current_stream())
+        return out
+
+    def hash_host(self, data_host: np.ndarray, stream=None) -> np.ndarray:
+        """Digest of a host buffer (copied in pieces by the library)."""
+        import torch
+        data_host = np.ascontiguousarray(data_host).view(np.uint8).reshape(-1)
+        dig = np.zeros(self.k, dtype=np.uint64)
+        _abi().ht_hash_host(self.ctx, data_host.ctypes.data if data_host.size else None,
+                         data_host.size, dig.ctypes.data,
+                         stream if stream is not None else torch.cuda.current_stream())
+        return dig
+
+    def status(self, stream=None):
+        _abi().ht_ctx_status(self.ctx, stream)
+
+    def launches(self) -> int:
+        return _abi().ht_ctx_launches(self.ctx)

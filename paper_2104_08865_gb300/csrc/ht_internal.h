@@ -1,0 +1,84 @@
+// ht_internal.h -- structures shared by the host runtime and the kernels of
+// libhalftime (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ht {
+
+// One string of a launch, as the planner lays it out.
+struct StrPlan {
+  const uint8_t *ptr;  // first byte of the string (device)
+  uint64_t len;        // bytes
+  uint64_t n_exec;     // N = floor(len / exec_bytes): EHC executions
+  uint64_t item0;      // first global work item of this string
+  uint64_t grp0;       // first tree-group slot of this string in scratch
+  uint32_t n_items;    // work items: max(1, ceil(N / 8^L))
+  uint32_t pad;
+};
+
+// Launch-wide control words (one per context).  cursor and exit return to 0
+// at the end of every hash launch; status is sticky until the host reads it.
+struct Ctl {
+  unsigned long long cursor;  // next work item to hand out
+  unsigned long long total;   // work items of the current batch (planner)
+  unsigned long long groups;  // tree-group slots the batch needs (planner)
+  unsigned int exit;          // warps that have left the work loop
+  unsigned int status;        // 0 or kStatusTooLong
+};
+constexpr unsigned int kStatusTooLong = 1;
+
+// Device scratch of one context.
+struct Scratch {
+  unsigned long long *grp_acc;  // [cap_groups][k][8] node accumulators
+  unsigned int *grp_cnt;        // [cap_groups] arrivals per group
+  unsigned long long *str_acc;  // [cap_strings][k] pending-root sums
+  unsigned int *str_done;       // [cap_strings] finished items per string
+  Ctl *ctl;
+  uint64_t cap_groups;
+};
+
+// Kernel parameters (passed as a __grid_constant__ struct: the hash keys of
+// the EHC step become constant-bank operands of the integer instructions).
+struct KParams {
+  unsigned long long E[30];     // EHC hash keys, e*w words
+  unsigned long long T0[5][8];  // level-0 tree keys per tree (7 used)
+  const unsigned long long *seeds;  // all seed words on the device
+  Scratch scr;
+  const StrPlan *plans;         // batch mode: planner output
+  const unsigned long long *item0s;  // batch mode: item0 of each string (+ total)
+  unsigned long long *digests;  // count * k words
+  StrPlan single;               // single-string mode: the string
+  unsigned long long item_begin, item_end;  // single mode: item range of this launch
+  unsigned int count;           // batch mode: strings
+  unsigned int total_warps;     // warps in the grid (exit protocol)
+};
+
+struct PlanArgs {
+  const void *const *ptrs;
+  const uint64_t *lens;
+  unsigned int count;
+  StrPlan *plans;
+  unsigned long long *item0s;
+  Ctl *ctl;
+  uint64_t cap_groups;
+};
+
+// Kernel variants of one width: chunk height L in {2, 3}; single-string or
+// batch; batch kernels also carry the unaligned-load path.
+struct KernelSet {
+  const void *single_aligned[2];    // [L-2]
+  const void *single_unaligned[2];  // [L-2]
+  const void *batch[2];             // [L-2]
+  const void *plan[2];              // [L-2]
+  int exec_bytes, k, n_seed, off_T, off_F, off_R, ew;
+};
+
+const KernelSet &kernels_w16();
+const KernelSet &kernels_w24();
+const KernelSet &kernels_w32();
+const KernelSet &kernels_w40();
+
+}  // namespace ht

@@ -1,0 +1,570 @@
+// ht_kernel.cuh -- the HalftimeHash hot path for sm_103a (arXiv 2104.08865).
+//
+// One warp hashes one "chunk": 8^L consecutive EHC executions of one string
+// (L = 2 or 3).  Inside the chunk:
+//   thread (x, p), x = lane>>2 in 0..7, p = lane&3 in 0..3, owns block lanes
+//   2p and 2p+1 (one 16-byte load covers both) of executions 8x..8x+7 of
+//   every 64-execution sub-chunk;
+//   * EHC (Section 3.3, Section 5.1): 128-bit streaming loads, XOR-only
+//     GF(8) encode, NH with mul.wide.u32 multiply-adds against keys held in
+//     the constant bank, combine with the paper's small matrices;
+//   * tree level 1 (Section 3.2 node variant, f = 8) in registers, level 2
+//     by warp shuffles across the eight x-threads, level 3 (L = 3) in
+//     registers again;
+// Above the chunk, levels are finished across warps without waiting: every
+// child adds its NH term of the parent (a sum, so order does not matter) into
+// the parent's accumulator with 64-bit atomics and bumps the parent's arrival
+// counter; the eighth arrival owns the parent and climbs on.  Nodes that can
+// never complete (the base-8 digits of N, Eq. stack-construction) are folded
+// straight into the string's final-NH sum (Section 5.2).  The warp that
+// finishes a string's last work item adds the Toeplitz tail NH (Section 6.1)
+// and writes the digest.  No kernel ever spins on another warp.
+#pragma once
+
+#include "ht_internal.h"
+#include "ht_spec.cuh"
+
+namespace ht {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---- arithmetic -------------------------------------------------------------
+
+// NH of one 64-bit word (lo, hi) against one key word: (lo + s.lo)(hi + s.hi)
+// with 32-bit sums and a 64-bit product (Section 3.2).
+__device__ __forceinline__ uint64_t nh(uint32_t lo, uint32_t hi, uint64_t s) {
+  return (uint64_t)(lo + (uint32_t)s) * (uint64_t)(hi + (uint32_t)(s >> 32));
+}
+__device__ __forceinline__ uint64_t nh64(uint64_t x, uint64_t s) {
+  return nh((uint32_t)x, (uint32_t)(x >> 32), s);
+}
+
+__device__ __forceinline__ uint64_t warp_sum(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Sum over the eight x-threads that share p (lane bits 2..4).
+__device__ __forceinline__ uint64_t x_sum(uint64_t v) {
+  v += __shfl_xor_sync(kFull, v, 4);
+  v += __shfl_xor_sync(kFull, v, 8);
+  v += __shfl_xor_sync(kFull, v, 16);
+  return v;
+}
+
+__device__ __forceinline__ uint64_t ld_cg(const unsigned long long *p) {
+  return __ldcg(p);
+}
+
+// ---- loads ----------------------------------------------------------------------
+
+// 16 bytes of input read once: no L1 allocation.
+__device__ __forceinline__ uint4 ld_stream(const uint8_t *p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+}
+
+// 16 bytes at an address that is not 16-byte aligned (sh = address & 15,
+// 1..15): two aligned loads of the granules the bytes straddle, realigned
+// with funnel shifts.  Both granules hold bytes of the request, so nothing
+// outside the string's 16-byte granules is touched.
+__device__ __forceinline__ uint4 ld_unaligned(const uint8_t *p, uint32_t sh) {
+  const uint8_t *b = p - sh;
+  const uint4 a = ld_stream(b), c = ld_stream(b + 16);
+  const uint32_t w[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+  uint32_t u[8], v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) u[j] = (sh & 8u) ? w[j + 2 < 8 ? j + 2 : 7] : w[j];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = (sh & 4u) ? u[j + 1 < 8 ? j + 1 : 7] : u[j];
+  const uint32_t r = (sh & 3u) * 8u;
+  uint4 o;
+  o.x = __funnelshift_r(v[0], v[1], r);
+  o.y = __funnelshift_r(v[1], v[2], r);
+  o.z = __funnelshift_r(v[2], v[3], r);
+  o.w = __funnelshift_r(v[3], v[4], r);
+  return o;
+}
+
+template <bool ALIGNED>
+__device__ __forceinline__ uint4 ld16(const uint8_t *p, uint32_t sh) {
+  if (ALIGNED) return ld_stream(p);
+  return sh == 0 ? ld_stream(p) : ld_unaligned(p, sh);
+}
+
+// One little-endian word of the tail holding nb (1..8) bytes starting at p.
+__device__ __forceinline__ uint64_t tail_word(const uint8_t *p, uint32_t nb) {
+  if (nb == 8 && (((uintptr_t)p) & 7u) == 0)
+    return __ldg(reinterpret_cast<const unsigned long long *>(p));
+  uint64_t w = 0;
+  for (uint32_t i = 0; i < nb; ++i) w |= (uint64_t)__ldg(p + i) << (8 * i);
+  return w;
+}
+
+// ---- EHC ------------------------------------------------------------------------
+
+// One EHC execution for block lanes 2p and 2p+1 (Section 3.3, Section 5.1):
+// Encode (systematic GF(8) code, XOR only), Hash (NH of every encoded word
+// under its own key E[c*3+u]), Combine (y = T h over Z_{2^64}).
+template <int W, bool ALIGNED>
+__device__ __forceinline__ void ehc2(const uint8_t *ex, int p, uint32_t sh,
+                                     const KParams &P, uint64_t (&y)[2][Spec<W>::k]) {
+  using S = Spec<W>;
+  constexpr int d = S::d, e = S::e, k = S::k, np = e - d, dw = d * kItemWords;
+  uint4 v[dw];
+#pragma unroll
+  for (int b = 0; b < dw; ++b) v[b] = ld16<ALIGNED>(ex + b * 64 + p * 16, sh);
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    uint32_t lo[dw], hi[dw];
+#pragma unroll
+    for (int b = 0; b < dw; ++b) {
+      lo[b] = l ? v[b].z : v[b].x;
+      hi[b] = l ? v[b].w : v[b].y;
+    }
+    uint64_t h[e];
+#pragma unroll
+    for (int c = 0; c < d; ++c) {
+      h[c] = nh(lo[3 * c], hi[3 * c], P.E[3 * c]);
+      h[c] += nh(lo[3 * c + 1], hi[3 * c + 1], P.E[3 * c + 1]);
+      h[c] += nh(lo[3 * c + 2], hi[3 * c + 2], P.E[3 * c + 2]);
+    }
+#pragma unroll
+    for (int r = 0; r < np; ++r) {
+      h[d + r] = 0;
+#pragma unroll
+      for (int pv = 0; pv < 3; ++pv) {
+        uint32_t plo = 0, phi = 0;
+#pragma unroll
+        for (int i = 0; i < d; ++i)
+#pragma unroll
+          for (int u = 0; u < 3; ++u)
+            if (gf8_feeds(S::A(i, r), u, pv)) {
+              plo ^= lo[3 * i + u];
+              phi ^= hi[3 * i + u];
+            }
+        h[d + r] += nh(plo, phi, P.E[3 * (d + r) + pv]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < k; ++t) {
+      uint64_t acc = 0;
+#pragma unroll
+      for (int c = 0; c < e; ++c) {
+        if (S::T(t, c) == 1) acc += h[c];
+        else if (S::T(t, c) != 0) acc += (uint64_t)S::T(t, c) * h[c];
+      }
+      y[l][t] = acc;
+    }
+  }
+}
+
+// ---- seeds ----------------------------------------------------------------------
+
+template <int W>
+__device__ __forceinline__ uint64_t tree_key(const KParams &P, int t, int lvl, int i) {
+  return __ldg(P.seeds + Dims<W>::off_T + (t * kLevels + lvl) * (kFan - 1) + i);
+}
+template <int W>
+__device__ __forceinline__ uint64_t final_key(const KParams &P, int t, int lvl, uint64_t j, int lane) {
+  return __ldg(P.seeds + Dims<W>::off_F + ((t * kLevels + lvl) * kFan + (int)j) * kLanes + lane);
+}
+
+// ---- the finaliser: pending-root sum + Toeplitz tail (Section 6.1) ----------
+
+template <int W>
+__device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx, int ln) {
+  constexpr int k = Spec<W>::k;
+  constexpr int B = Dims<W>::exec_bytes;
+  __threadfence();
+  uint64_t acc[k];
+#pragma unroll
+  for (int t = 0; t < k; ++t) acc[t] = ld_cg(P.scr.str_acc + (uint64_t)sidx * k + t);
+  const uint64_t tstart = sp.n_exec * (uint64_t)B;
+  const uint64_t tlen = sp.len - tstart;  // < B
+  const uint32_t M = (uint32_t)((tlen + 7) / 8);
+  uint64_t sum[k];
+#pragma unroll
+  for (int t = 0; t < k; ++t) sum[t] = 0;
+  for (uint32_t m = ln; m <= M; m += 32) {
+    uint64_t word;
+    if (m == M) {
+      word = sp.len;
+    } else {
+      const uint64_t rem = tlen - 8ull * m;
+      word = tail_word(sp.ptr + tstart + 8ull * m, rem < 8 ? (uint32_t)rem : 8u);
+    }
+#pragma unroll
+    for (int t = 0; t < k; ++t) sum[t] += nh64(word, __ldg(P.seeds + Dims<W>::off_R + t + m));
+  }
+#pragma unroll
+  for (int t = 0; t < k; ++t) sum[t] = warp_sum(sum[t]);
+  if (ln == 0) {
+#pragma unroll
+    for (int t = 0; t < k; ++t) {
+      P.digests[(uint64_t)sidx * k + t] = acc[t] + sum[t];
+      P.scr.str_acc[(uint64_t)sidx * k + t] = 0;
+    }
+    P.scr.str_done[sidx] = 0;
+  }
+}
+
+// ---- one work item: a chunk of 8^L executions ---------------------------------
+
+template <int W, int L, bool ALIGNED>
+__device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
+                           uint64_t c, int ln) {
+  constexpr int k = Spec<W>::k;
+  constexpr uint64_t B = Dims<W>::exec_bytes;
+  constexpr uint64_t CH = 1ull << (3 * L);
+  const int x = ln >> 2, p = ln & 3;
+  const uint64_t N = sp.n_exec;
+  const uint32_t sh = ALIGNED ? 0u : (uint32_t)(((uintptr_t)sp.ptr) & 15u);
+
+  uint64_t pend[k];  // this thread's share of the final-NH sum
+#pragma unroll
+  for (int t = 0; t < k; ++t) pend[t] = 0;
+  bool anyp = false;
+
+  const uint64_t e0 = c * CH;
+  if (e0 < N) {
+    const bool full = (N - e0) >= CH;
+    uint64_t root[2][k];
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+#pragma unroll
+      for (int t = 0; t < k; ++t) root[l][t] = 0;
+    constexpr int NSUB = (L == 3) ? 8 : 1;
+#pragma unroll 1
+    for (int sub = 0; sub < NSUB; ++sub) {
+      const uint64_t sb = e0 + 64ull * sub;
+      if (sb >= N) break;
+      const int m = (int)((N - sb) < 64 ? (N - sb) : 64);
+      int cnt = m - 8 * x;
+      cnt = cnt < 0 ? 0 : (cnt > 8 ? 8 : cnt);
+      uint64_t n1[2][k];
+#pragma unroll
+      for (int l = 0; l < 2; ++l)
+#pragma unroll
+        for (int t = 0; t < k; ++t) n1[l][t] = 0;
+      const uint8_t *ex = sp.ptr + (sb + 8ull * x) * B;
+      if (cnt == 8) {
+        // eight leaves -> one level-1 node per (tree, lane), in registers
+#pragma unroll 1
+        for (int s = 0; s < 8; ++s) {
+          uint64_t y[2][k];
+          ehc2<W, ALIGNED>(ex + s * B, p, sh, P, y);
+#pragma unroll
+          for (int l = 0; l < 2; ++l)
+#pragma unroll
+            for (int t = 0; t < k; ++t)
+              n1[l][t] += (s < 7) ? nh64(y[l][t], P.T0[t][s]) : y[l][t];
+        }
+      } else {
+        // the last, incomplete group of leaves: pending at level 0, slot s
+#pragma unroll 1
+        for (int s = 0; s < cnt; ++s) {
+          uint64_t y[2][k];
+          ehc2<W, ALIGNED>(ex + s * B, p, sh, P, y);
+#pragma unroll
+          for (int t = 0; t < k; ++t)
+            pend[t] += nh64(y[0][t], final_key<W>(P, t, 0, s, 2 * p)) +
+                       nh64(y[1][t], final_key<W>(P, t, 0, s, 2 * p + 1));
+          anyp = true;
+        }
+      }
+      if (m == 64) {
+        // level 2 across the eight x-threads
+        uint64_t n2[2][k];
+#pragma unroll
+        for (int t = 0; t < k; ++t) {
+          const uint64_t key = x < 7 ? tree_key<W>(P, t, 1, x) : 0;
+#pragma unroll
+          for (int l = 0; l < 2; ++l)
+            n2[l][t] = x_sum(x < 7 ? nh64(n1[l][t], key) : n1[l][t]);
+        }
+        if (L == 2) {
+#pragma unroll
+          for (int l = 0; l < 2; ++l)
+#pragma unroll
+            for (int t = 0; t < k; ++t) root[l][t] = n2[l][t];
+        } else if (full) {
+#pragma unroll
+          for (int t = 0; t < k; ++t) {
+            const uint64_t key = sub < 7 ? tree_key<W>(P, t, 2, sub) : 0;
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+              root[l][t] += sub < 7 ? nh64(n2[l][t], key) : n2[l][t];
+          }
+        } else {
+          // a complete level-2 node of an incomplete chunk: pending, slot sub.
+          // n2 is the same in all eight x-threads: thread x takes tree t = x.
+#pragma unroll
+          for (int t = 0; t < k; ++t)
+            if (x == t)
+              pend[t] += nh64(n2[0][t], final_key<W>(P, t, 2, sub, 2 * p)) +
+                         nh64(n2[1][t], final_key<W>(P, t, 2, sub, 2 * p + 1));
+          anyp = true;
+        }
+      } else if (cnt == 8) {
+        // complete level-1 node of an incomplete sub-chunk: pending, slot x
+#pragma unroll
+        for (int t = 0; t < k; ++t)
+          pend[t] += nh64(n1[0][t], final_key<W>(P, t, 1, x, 2 * p)) +
+                     nh64(n1[1][t], final_key<W>(P, t, 1, x, 2 * p + 1));
+        anyp = true;
+      }
+    }
+
+    if (full) {
+      // climb from the chunk root (level L, index c); thread x owns tree x
+      uint64_t v0 = 0, v1 = 0;
+#pragma unroll
+      for (int t = 0; t < k; ++t)
+        if (x == t) {
+          v0 = root[0][t];
+          v1 = root[1][t];
+        }
+      int lvl = L;
+      uint64_t idx = c, goff = 0;
+      for (;;) {
+        const uint64_t C = N >> (3 * lvl);
+        const uint64_t first_pending = C & ~7ull;
+        if (idx >= first_pending) {
+          const uint64_t j = idx - first_pending;
+#pragma unroll
+          for (int t = 0; t < k; ++t)
+            if (x == t)
+              pend[t] += nh64(v0, final_key<W>(P, t, lvl, j, 2 * p)) +
+                         nh64(v1, final_key<W>(P, t, lvl, j, 2 * p + 1));
+          anyp = true;
+          break;
+        }
+        const uint64_t g = idx >> 3;
+        const int pos = (int)(idx & 7);
+        const uint64_t slot = sp.grp0 + goff + g;
+        unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
+        if (x < k) {
+          uint64_t a0 = v0, a1 = v1;
+          if (pos < 7) {
+            const uint64_t key = tree_key<W>(P, x, lvl, pos);
+            a0 = nh64(v0, key);
+            a1 = nh64(v1, key);
+          }
+          atomicAdd(acc, (unsigned long long)a0);
+          atomicAdd(acc + 1, (unsigned long long)a1);
+        }
+        __threadfence();
+        __syncwarp();
+        unsigned old = 0;
+        if (ln == 0) old = atomicAdd(P.scr.grp_cnt + slot, 1u);
+        old = __shfl_sync(kFull, old, 0);
+        if (old != kFan - 1) break;
+        // eighth arrival: the parent node is complete and ours
+        __threadfence();
+        if (x < k) {
+          v0 = ld_cg(acc);
+          v1 = ld_cg(acc + 1);
+          acc[0] = 0;
+          acc[1] = 0;
+        }
+        if (ln == 0) P.scr.grp_cnt[slot] = 0;
+        goff += C >> 3;
+        lvl += 1;
+        idx = g;
+      }
+    }
+  }
+
+  if (__any_sync(kFull, anyp)) {
+#pragma unroll
+    for (int t = 0; t < k; ++t) pend[t] = warp_sum(pend[t]);
+    if (ln == 0)
+#pragma unroll
+      for (int t = 0; t < k; ++t)
+        if (pend[t]) atomicAdd(P.scr.str_acc + (uint64_t)sidx * k + t, (unsigned long long)pend[t]);
+  }
+  __threadfence();
+  __syncwarp();
+  unsigned old = 0;
+  if (ln == 0) old = atomicAdd(P.scr.str_done + sidx, 1u);
+  old = __shfl_sync(kFull, old, 0);
+  if (old == sp.n_items - 1) finish_string<W>(P, sp, sidx, ln);
+}
+
+// ---- the persistent kernel ----------------------------------------------------
+
+__device__ __forceinline__ unsigned find_string(const unsigned long long *item0s,
+                                                unsigned count, uint64_t item) {
+  unsigned lo = 0, hi = count;  // item0s[lo] <= item < item0s[hi]
+  while (hi - lo > 1) {
+    const unsigned mid = (lo + hi) >> 1;
+    if (__ldg(item0s + mid) <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void exit_protocol(const KParams &P, int ln) {
+  __syncwarp();
+  if (ln == 0) {
+    __threadfence();
+    const unsigned old = atomicAdd(&P.scr.ctl->exit, 1u);
+    if (old == P.total_warps - 1) {
+      // every warp has made its last grab: rearm for the next launch
+      P.scr.ctl->cursor = 0;
+      P.scr.ctl->exit = 0;
+      __threadfence();
+    }
+  }
+}
+
+template <int W, int L, bool SINGLE, bool ALIGNED>
+__global__ void __launch_bounds__(256) hash_kernel(const __grid_constant__ KParams P) {
+  const int ln = threadIdx.x & 31;
+  uint64_t total;
+  if (SINGLE) {
+    total = P.item_end;
+  } else {
+    if (__ldcg(&P.scr.ctl->status) != 0) {
+      exit_protocol(P, ln);
+      return;
+    }
+    total = __ldcg(&P.scr.ctl->total);
+  }
+  for (;;) {
+    unsigned long long item = 0;
+    if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if (SINGLE) item += P.item_begin;
+    if (item >= total) break;
+    if (SINGLE) {
+      hash_chunk<W, L, ALIGNED>(P, P.single, 0, item, ln);
+    } else {
+      const unsigned s = find_string(P.item0s, P.count, item);
+      const StrPlan sp = P.plans[s];
+      const uint64_t c = item - sp.item0;
+      if ((((uintptr_t)sp.ptr) & 15u) == 0)
+        hash_chunk<W, L, true>(P, sp, s, c, ln);
+      else
+        hash_chunk<W, L, false>(P, sp, s, c, ln);
+    }
+  }
+  exit_protocol(P, ln);
+}
+
+// ---- the batch planner (one block) ---------------------------------------------
+
+template <int W, int L>
+__global__ void __launch_bounds__(1024) plan_kernel(const PlanArgs A) {
+  constexpr uint64_t B = Dims<W>::exec_bytes;
+  __shared__ unsigned long long s_items[32], s_groups[32];
+  const unsigned tid = threadIdx.x, nt = blockDim.x;
+  const unsigned per = (A.count + nt - 1) / nt;
+  const unsigned lo = tid * per < A.count ? tid * per : A.count;
+  const unsigned hi = lo + per < A.count ? lo + per : A.count;
+  auto groups_of = [](uint64_t N) {
+    uint64_t g = 0;
+    for (int lvl = L; lvl < kLevels; ++lvl) g += N >> (3 * lvl + 3);
+    return g;
+  };
+  auto items_of = [](uint64_t N) {
+    const uint64_t it = (N + (1ull << (3 * L)) - 1) >> (3 * L);
+    return it ? it : 1ull;
+  };
+  unsigned long long my_items = 0, my_groups = 0;
+  for (unsigned i = lo; i < hi; ++i) {
+    const uint64_t N = A.lens[i] / B;
+    my_items += items_of(N);
+    my_groups += groups_of(N);
+  }
+  // block-wide exclusive scan of (items, groups)
+  const int ln = tid & 31, wid = tid >> 5;
+  unsigned long long xi = my_items, xg = my_groups;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long yi = __shfl_up_sync(kFull, xi, o);
+    const unsigned long long yg = __shfl_up_sync(kFull, xg, o);
+    if (ln >= o) {
+      xi += yi;
+      xg += yg;
+    }
+  }
+  if (ln == 31) {
+    s_items[wid] = xi;
+    s_groups[wid] = xg;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned nw = nt >> 5;
+    unsigned long long vi = ln < (int)nw ? s_items[ln] : 0, vg = ln < (int)nw ? s_groups[ln] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long yi = __shfl_up_sync(kFull, vi, o);
+      const unsigned long long yg = __shfl_up_sync(kFull, vg, o);
+      if (ln >= o) {
+        vi += yi;
+        vg += yg;
+      }
+    }
+    if (ln < (int)nw) {
+      s_items[ln] = vi;
+      s_groups[ln] = vg;
+    }
+  }
+  __syncthreads();
+  unsigned long long base_i = (xi - my_items) + (wid ? s_items[wid - 1] : 0);
+  unsigned long long base_g = (xg - my_groups) + (wid ? s_groups[wid - 1] : 0);
+  for (unsigned i = lo; i < hi; ++i) {
+    const uint64_t len = A.lens[i];
+    const uint64_t N = len / B;
+    StrPlan sp;
+    sp.ptr = static_cast<const uint8_t *>(A.ptrs[i]);
+    sp.len = len;
+    sp.n_exec = N;
+    sp.item0 = base_i;
+    sp.grp0 = base_g;
+    sp.n_items = (uint32_t)items_of(N);
+    sp.pad = 0;
+    A.plans[i] = sp;
+    A.item0s[i] = base_i;
+    base_i += items_of(N);
+    base_g += groups_of(N);
+  }
+  if (tid == nt - 1) {
+    const unsigned long long total_i = s_items[(nt >> 5) - 1];
+    const unsigned long long total_g = s_groups[(nt >> 5) - 1];
+    A.item0s[A.count] = total_i;
+    A.ctl->total = total_i;
+    A.ctl->groups = total_g;
+    if (total_g > A.cap_groups) A.ctl->status = kStatusTooLong;
+  }
+}
+
+// ---- kernel tables --------------------------------------------------------------
+
+template <int W>
+KernelSet make_kernel_set() {
+  KernelSet ks;
+  ks.single_aligned[0] = (const void *)hash_kernel<W, 2, true, true>;
+  ks.single_aligned[1] = (const void *)hash_kernel<W, 3, true, true>;
+  ks.single_unaligned[0] = (const void *)hash_kernel<W, 2, true, false>;
+  ks.single_unaligned[1] = (const void *)hash_kernel<W, 3, true, false>;
+  ks.batch[0] = (const void *)hash_kernel<W, 2, false, false>;
+  ks.batch[1] = (const void *)hash_kernel<W, 3, false, false>;
+  ks.plan[0] = (const void *)plan_kernel<W, 2>;
+  ks.plan[1] = (const void *)plan_kernel<W, 3>;
+  ks.exec_bytes = Dims<W>::exec_bytes;
+  ks.k = Spec<W>::k;
+  ks.n_seed = Dims<W>::n_seed;
+  ks.off_T = Dims<W>::off_T;
+  ks.off_F = Dims<W>::off_F;
+  ks.off_R = Dims<W>::off_R;
+  ks.ew = Dims<W>::ew;
+  return ks;
+}
+
+}  // namespace ht

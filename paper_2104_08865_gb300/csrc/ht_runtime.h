@@ -1,0 +1,58 @@
+// ht_runtime.h -- host-side state of a libhalftime context (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <vector>
+
+#include "halftime.h"
+#include "ht_internal.h"
+
+constexpr int kStageSlots = 4;  // staging ring of ht_hash_host
+
+struct ht_ctx {
+  int width = 0;
+  int device = 0;
+  int num_sms = 1;
+  const ht::KernelSet *ks = nullptr;
+  std::vector<uint64_t> h_seeds;
+  unsigned long long *d_seeds = nullptr;
+  uint64_t *d_digest = nullptr;  // k words, for host-side calls
+  // scratch (see ht::Scratch)
+  unsigned long long *grp_acc = nullptr;
+  unsigned int *grp_cnt = nullptr;
+  unsigned long long *str_acc = nullptr;
+  unsigned int *str_done = nullptr;
+  ht::StrPlan *plans = nullptr;
+  unsigned long long *item0s = nullptr;
+  ht::Ctl *ctl = nullptr;
+  uint64_t cap_groups = 0, cap_strings = 0;
+  // launch shapes: [0..63] by floor(log2(len)), [64] batches
+  ht_shape shapes[65];
+  // batch graph: planner -> persistent kernel
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraphNode_t node_plan = nullptr, node_hash = nullptr;
+  cudaKernelNodeParams node_hash_params = {};
+  ht_shape graph_shape = {};
+  bool graph_valid = false;
+  ht::PlanArgs plan_args = {};
+  ht::KParams batch_params = {};
+  // host-input pipeline
+  cudaStream_t copy_stream = nullptr;
+  uint8_t *stage[kStageSlots] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t stage_bytes = 0;
+  cudaEvent_t ev_copy[kStageSlots] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_hash[kStageSlots] = {nullptr, nullptr, nullptr, nullptr};
+  std::atomic<uint64_t> launches{0};
+};
+
+namespace ht {
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+const KernelSet *kernel_set(int width);
+uint64_t items_of(uint64_t N, int L);
+uint64_t groups_of(uint64_t N, int L);
+}  // namespace ht

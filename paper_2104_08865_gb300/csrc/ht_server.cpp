@@ -1,0 +1,555 @@
+// ht_server.cpp -- continuous-batching request loop of libhalftime.
+//
+// Requests arrive on any thread (ht_server_submit).  A dispatcher thread turns
+// the head of the FIFO queue into a batch as soon as a stream slot is free,
+// admitting requests while their bytes fit the memory budget; pinned-host
+// requests are staged into a device arena carved from that budget.  Each slot
+// owns its own context (so its tree scratch never races another slot's), its
+// stream and pinned descriptor buffers; a batch is one ht_hash_batch (planner
+// + persistent kernel replayed from a graph) followed by a digest copy and an
+// event.  A completion thread retires batches as their events fire, copies
+// digests to the callers, frees budget and arena space, records latencies and
+// wakes the dispatcher and any waiters.  All waits on the host are bounded by
+// the caller's timeout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "halftime.h"
+#include "halftime_testing.h"
+#include "ht_runtime.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
+}
+
+enum ReqState { kQueued = 0, kInFlight = 1, kDone = 2 };
+
+struct Req {
+  const void *ptr = nullptr;
+  uint64_t len = 0;
+  int pinned = 0;
+  uint64_t *digest_host = nullptr;
+  int64_t t_arrive = 0, t_launch = 0, t_done = 0;
+  int state = kQueued;
+  int status = HT_OK;
+  uint64_t arena_off = 0;
+  bool has_arena = false;
+};
+
+// First-fit allocator over [0, size) with 256-byte granules.
+class Arena {
+ public:
+  void reset(uint64_t size) {
+    free_.clear();
+    if (size) free_[0] = size;
+  }
+  bool alloc(uint64_t bytes, uint64_t *off) {
+    bytes = std::max<uint64_t>(256, (bytes + 255) & ~255ull);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const uint64_t rest = it->second - bytes, start = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t bytes) {
+    bytes = std::max<uint64_t>(256, (bytes + 255) & ~255ull);
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+
+ private:
+  std::map<uint64_t, uint64_t> free_;
+};
+
+struct Slot {
+  bool busy = false;      // owns a batch
+  bool launched = false;  // its work is enqueued: safe to poll
+  cudaStream_t stream = nullptr;
+  ht_ctx *ctx = nullptr;
+  cudaEvent_t ev = nullptr;
+  const void **h_ptrs = nullptr;
+  uint64_t *h_lens = nullptr;
+  uint64_t *h_digests = nullptr;
+  const void **d_ptrs = nullptr;
+  uint64_t *d_lens = nullptr;
+  uint64_t *d_digests = nullptr;
+  std::vector<uint64_t> tickets;
+  uint64_t bytes = 0;
+  int64_t fake_deadline = 0;
+  bool fake_fail = false;
+  int launch_status = HT_OK;
+};
+
+}  // namespace
+
+struct ht_server {
+  // configuration
+  int width = 0, k = 0;
+  bool fake = false;
+  uint64_t fake_delay_us = 0;
+  int64_t fake_fail_batch = -1;
+  uint64_t budget = 0;
+  ht_server_opts opts = {};
+  // device resources
+  uint8_t *arena_base = nullptr;
+  Arena arena;
+  std::vector<Slot> slots;
+  // state
+  std::mutex mu;
+  std::condition_variable cv_dispatch, cv_complete, cv_done;
+  std::deque<Req> reqs;  // index = ticket
+  std::deque<uint64_t> queue;
+  uint64_t in_use = 0;
+  uint64_t batches = 0, rejected = 0, completed = 0, bytes_completed = 0;
+  std::vector<double> lat_us;
+  int64_t first_arrive = 0, last_done = 0;
+  bool stop = false;
+  std::thread dispatcher, completer;
+};
+
+namespace {
+
+// Enqueues copies, the batch hash and the digest copy of a formed batch.
+int launch_real(ht_server *S, Slot &sl, const std::vector<Req *> &batch) {
+  const size_t n = batch.size();
+  for (size_t i = 0; i < n; ++i) {
+    Req *r = batch[i];
+    if (r->pinned && r->len) {
+      uint8_t *dst = S->arena_base + r->arena_off;
+      cudaError_t e = cudaMemcpyAsync(dst, r->ptr, r->len, cudaMemcpyHostToDevice, sl.stream);
+      if (e != cudaSuccess) return ht::cuda_error(e, "request staging copy");
+      sl.h_ptrs[i] = dst;
+    } else {
+      sl.h_ptrs[i] = r->ptr;
+    }
+    sl.h_lens[i] = r->len;
+  }
+  cudaError_t e = cudaMemcpyAsync(sl.d_ptrs, sl.h_ptrs, n * sizeof(void *), cudaMemcpyHostToDevice, sl.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sl.d_lens, sl.h_lens, n * sizeof(uint64_t), cudaMemcpyHostToDevice, sl.stream);
+  if (e != cudaSuccess) return ht::cuda_error(e, "batch descriptor copy");
+  int rc = ht_hash_batch(sl.ctx, sl.d_ptrs, sl.d_lens, n, sl.d_digests, sl.stream);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(sl.h_digests, sl.d_digests, n * S->k * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                      sl.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
+  if (e != cudaSuccess) return ht::cuda_error(e, "batch digest copy");
+  return HT_OK;
+}
+
+// 1 = finished, 0 = running, < 0 = error.
+int poll_slot(ht_server *S, Slot &sl) {
+  if (sl.launch_status != HT_OK) return sl.launch_status;
+  if (S->fake) {
+    if (now_ns() < sl.fake_deadline) return 0;
+    return sl.fake_fail ? ht::set_error(HT_ERR_CUDA, "injected batch failure") : 1;
+  }
+  cudaError_t e = cudaEventQuery(sl.ev);
+  if (e == cudaErrorNotReady) return 0;
+  if (e != cudaSuccess) return ht::cuda_error(e, "batch event");
+  return 1;
+}
+
+void release_req(ht_server *S, Req &r) {
+  if (r.has_arena) {
+    S->arena.release(r.arena_off, r.len);
+    r.has_arena = false;
+  }
+  S->in_use -= r.len;
+}
+
+void dispatcher_main(ht_server *S) {
+  if (!S->fake && !S->slots.empty()) cudaSetDevice(S->slots[0].ctx->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    Slot *free_slot = nullptr;
+    S->cv_dispatch.wait(lk, [&] {
+      if (S->stop) return true;
+      if (S->queue.empty()) return false;
+      for (auto &sl : S->slots)
+        if (!sl.busy) return true;
+      return false;
+    });
+    if (S->stop) break;
+    // optional batching window: wait a little for batch-mates
+    if (S->opts.max_wait_us && S->queue.size() < S->opts.max_batch) {
+      const int64_t oldest = S->reqs[S->queue.front()].t_arrive;
+      const int64_t until = oldest + (int64_t)S->opts.max_wait_us * 1000;
+      while (!S->stop && S->queue.size() < S->opts.max_batch && now_ns() < until)
+        S->cv_dispatch.wait_for(lk, std::chrono::nanoseconds(std::max<int64_t>(until - now_ns(), 1000)));
+      if (S->stop) break;
+      if (S->queue.empty()) continue;
+    }
+    for (auto &sl : S->slots)
+      if (!sl.busy) {
+        free_slot = &sl;
+        break;
+      }
+    if (!free_slot) continue;
+    std::vector<Req *> batch;
+    std::vector<uint64_t> tickets;
+    uint64_t bytes = 0;
+    while (!S->queue.empty() && batch.size() < S->opts.max_batch) {
+      Req &r = S->reqs[S->queue.front()];
+      if (S->in_use + r.len > S->budget) break;
+      if (r.pinned && r.len) {
+        if (!S->arena.alloc(r.len, &r.arena_off)) break;
+        r.has_arena = true;
+      }
+      S->in_use += r.len;
+      bytes += r.len;
+      r.state = kInFlight;
+      batch.push_back(&r);
+      tickets.push_back(S->queue.front());
+      S->queue.pop_front();
+    }
+    if (batch.empty()) {
+      // the head does not fit until in-flight work retires
+      S->cv_dispatch.wait_for(lk, std::chrono::milliseconds(1));
+      continue;
+    }
+    Slot &sl = *free_slot;
+    sl.busy = true;
+    sl.tickets = tickets;
+    sl.bytes = bytes;
+    const int64_t t = now_ns();
+    for (Req *r : batch) r->t_launch = t;
+    const uint64_t batch_no = S->batches++;
+    lk.unlock();
+    int rc = HT_OK;
+    if (S->fake) {
+      sl.fake_deadline = now_ns() + (int64_t)S->fake_delay_us * 1000;
+      sl.fake_fail = ((int64_t)batch_no == S->fake_fail_batch);
+      for (size_t i = 0; i < batch.size(); ++i)
+        memset(sl.h_digests + i * S->k, 0, S->k * sizeof(uint64_t));
+    } else {
+      rc = launch_real(S, sl, batch);
+    }
+    lk.lock();
+    sl.launch_status = rc;
+    sl.launched = true;
+    S->cv_complete.notify_all();
+  }
+}
+
+void completer_main(ht_server *S) {
+  if (!S->fake && !S->slots.empty()) cudaSetDevice(S->slots[0].ctx->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    bool any_busy = false;
+    for (auto &sl : S->slots) {
+      if (!sl.busy) continue;
+      any_busy = true;
+      if (!sl.launched) continue;
+      const int rc = poll_slot(S, sl);
+      if (rc == 0) continue;
+      const int64_t t = now_ns();
+      for (size_t i = 0; i < sl.tickets.size(); ++i) {
+        Req &r = S->reqs[sl.tickets[i]];
+        if (rc == 1 && r.digest_host) memcpy(r.digest_host, sl.h_digests + i * S->k, S->k * sizeof(uint64_t));
+        r.status = rc == 1 ? HT_OK : rc;
+        r.state = kDone;
+        r.t_done = t;
+        release_req(S, r);
+        if (rc == 1) {
+          S->completed++;
+          S->bytes_completed += r.len;
+          S->lat_us.push_back((r.t_done - r.t_arrive) / 1000.0);
+          if (!S->first_arrive || r.t_arrive < S->first_arrive) S->first_arrive = r.t_arrive;
+          S->last_done = std::max(S->last_done, t);
+        }
+      }
+      sl.tickets.clear();
+      sl.busy = false;
+      sl.launched = false;
+      sl.launch_status = HT_OK;
+      S->cv_dispatch.notify_all();
+      S->cv_done.notify_all();
+    }
+    if (S->stop && !any_busy) break;
+    if (!any_busy) {
+      S->cv_complete.wait_for(lk, std::chrono::milliseconds(2));
+    } else {
+      lk.unlock();
+      std::this_thread::yield();
+      lk.lock();
+    }
+  }
+}
+
+int make_server(ht_server *S, ht_ctx *ctx, uint64_t budget, const ht_server_opts *opts) {
+  S->budget = budget;
+  ht_server_opts o;
+  o.n_streams = 4;
+  o.max_batch = 4096;
+  o.max_queue = 1u << 20;
+  o.max_wait_us = 0;
+  if (opts) {
+    if (opts->n_streams > 0) o.n_streams = opts->n_streams;
+    if (opts->max_batch > 0) o.max_batch = opts->max_batch;
+    if (opts->max_queue > 0) o.max_queue = opts->max_queue;
+    o.max_wait_us = opts->max_wait_us;
+  }
+  S->opts = o;
+  S->slots.resize((size_t)o.n_streams);
+  if (S->fake) {
+    S->arena.reset(budget);
+    for (auto &sl : S->slots) sl.h_digests = new uint64_t[o.max_batch * S->k];
+    return HT_OK;
+  }
+  cudaError_t e = cudaMalloc((void **)&S->arena_base, std::max<uint64_t>(budget, 256));
+  if (e != cudaSuccess) return ht::cuda_error(e, "server arena");
+  S->arena.reset(budget);
+  for (auto &sl : S->slots) {
+    int rc = ht_ctx_create(ctx->width, ctx->h_seeds.data(), ctx->h_seeds.size(), nullptr, &sl.ctx);
+    if (rc) return rc;
+    rc = ht_ctx_reserve(sl.ctx, budget, o.max_batch);
+    if (rc) return rc;
+    sl.ctx->shapes[64] = ctx->shapes[64];
+    e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&sl.h_ptrs, o.max_batch * sizeof(void *));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&sl.h_lens, o.max_batch * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&sl.h_digests, o.max_batch * S->k * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sl.d_ptrs, o.max_batch * sizeof(void *));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sl.d_lens, o.max_batch * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sl.d_digests, o.max_batch * S->k * sizeof(uint64_t));
+    if (e != cudaSuccess) return ht::cuda_error(e, "server slot");
+  }
+  return HT_OK;
+}
+
+void free_server(ht_server *S) {
+  if (S->fake) {
+    for (auto &sl : S->slots) delete[] sl.h_digests;
+  } else {
+    for (auto &sl : S->slots) {
+      if (sl.stream) cudaStreamSynchronize(sl.stream);
+      if (sl.ctx) ht_ctx_destroy(sl.ctx);
+      if (sl.stream) cudaStreamDestroy(sl.stream);
+      if (sl.ev) cudaEventDestroy(sl.ev);
+      cudaFreeHost(sl.h_ptrs);
+      cudaFreeHost(sl.h_lens);
+      cudaFreeHost(sl.h_digests);
+      cudaFree(sl.d_ptrs);
+      cudaFree(sl.d_lens);
+      cudaFree(sl.d_digests);
+    }
+    cudaFree(S->arena_base);
+  }
+  delete S;
+}
+
+void start_threads(ht_server *S) {
+  S->dispatcher = std::thread(dispatcher_main, S);
+  S->completer = std::thread(completer_main, S);
+}
+
+double percentile(std::vector<double> v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double pos = q * (double)(v.size() - 1);
+  const size_t i = (size_t)pos;
+  const double f = pos - (double)i;
+  return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+int ht_server_create(ht_ctx *ctx, uint64_t budget_bytes, const ht_server_opts *opts, ht_server **out) {
+  if (!ctx || !out || budget_bytes == 0) return ht::set_error(HT_ERR_ARG, "ht_server_create: bad arguments");
+  *out = nullptr;
+  ht_server *S = new ht_server();
+  S->width = ctx->width;
+  S->k = ctx->ks->k;
+  int rc = make_server(S, ctx, budget_bytes, opts);
+  if (rc) {
+    free_server(S);
+    return rc;
+  }
+  start_threads(S);
+  *out = S;
+  return HT_OK;
+}
+
+int ht_server_create_fake(int width, uint64_t budget_bytes, const ht_server_opts *opts,
+                          uint64_t batch_delay_us, int64_t fail_batch, ht_server **out) {
+  if (width != 16 && width != 24 && width != 32 && width != 40)
+    return ht::set_error(HT_ERR_WIDTH, "unsupported width %d", width);
+  if (!out || budget_bytes == 0) return ht::set_error(HT_ERR_ARG, "ht_server_create_fake: bad arguments");
+  ht_server *S = new ht_server();
+  S->width = width;
+  S->k = width / 8;
+  S->fake = true;
+  S->fake_delay_us = batch_delay_us;
+  S->fake_fail_batch = fail_batch;
+  int rc = make_server(S, nullptr, budget_bytes, opts);
+  if (rc) {
+    free_server(S);
+    return rc;
+  }
+  start_threads(S);
+  *out = S;
+  return HT_OK;
+}
+
+int ht_server_submit(ht_server *S, const void *ptr, uint64_t len, int pinned, uint64_t *digest_host,
+                     uint64_t *ticket) {
+  if (!S || !ticket || !digest_host || (len && !ptr))
+    return ht::set_error(HT_ERR_ARG, "ht_server_submit: bad arguments");
+  if (len > S->budget) {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->rejected++;
+    return ht::set_error(HT_ERR_BUDGET, "request of %llu bytes exceeds the budget of %llu",
+                         (unsigned long long)len, (unsigned long long)S->budget);
+  }
+  std::lock_guard<std::mutex> g(S->mu);
+  if (S->queue.size() >= S->opts.max_queue) {
+    S->rejected++;
+    return ht::set_error(HT_ERR_BUSY, "server queue full");
+  }
+  Req r;
+  r.ptr = ptr;
+  r.len = len;
+  r.pinned = pinned ? 1 : 0;
+  r.digest_host = digest_host;
+  r.t_arrive = now_ns();
+  S->reqs.push_back(r);
+  *ticket = S->reqs.size() - 1;
+  S->queue.push_back(*ticket);
+  S->cv_dispatch.notify_one();
+  return HT_OK;
+}
+
+int ht_server_poll(ht_server *S, uint64_t ticket, int *done) {
+  if (!S || !done) return ht::set_error(HT_ERR_ARG, "ht_server_poll: bad arguments");
+  std::lock_guard<std::mutex> g(S->mu);
+  if (ticket >= S->reqs.size()) return ht::set_error(HT_ERR_ARG, "unknown ticket");
+  const Req &r = S->reqs[ticket];
+  *done = r.state == kDone;
+  return r.state == kDone ? r.status : HT_OK;
+}
+
+int ht_server_wait(ht_server *S, uint64_t ticket, uint64_t timeout_us) {
+  if (!S) return ht::set_error(HT_ERR_ARG, "ht_server_wait: NULL server");
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (ticket >= S->reqs.size()) return ht::set_error(HT_ERR_ARG, "unknown ticket");
+  const bool ok = S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us),
+                                      [&] { return S->reqs[ticket].state == kDone; });
+  if (!ok) return ht::set_error(HT_ERR_TIMEOUT, "request %llu not done after %llu us",
+                                (unsigned long long)ticket, (unsigned long long)timeout_us);
+  const int st = S->reqs[ticket].status;
+  if (st != HT_OK) return ht::set_error(st, "request %llu failed (%d)", (unsigned long long)ticket, st);
+  return HT_OK;
+}
+
+int ht_server_drain(ht_server *S, uint64_t timeout_us) {
+  if (!S) return ht::set_error(HT_ERR_ARG, "ht_server_drain: NULL server");
+  std::unique_lock<std::mutex> lk(S->mu);
+  const bool ok = S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] {
+    if (!S->queue.empty()) return false;
+    for (auto &sl : S->slots)
+      if (sl.busy) return false;
+    return true;
+  });
+  return ok ? HT_OK : ht::set_error(HT_ERR_TIMEOUT, "server not drained after %llu us",
+                                    (unsigned long long)timeout_us);
+}
+
+int ht_server_cancel(ht_server *S, uint64_t ticket) {
+  if (!S) return ht::set_error(HT_ERR_ARG, "ht_server_cancel: NULL server");
+  std::lock_guard<std::mutex> g(S->mu);
+  if (ticket >= S->reqs.size()) return ht::set_error(HT_ERR_ARG, "unknown ticket");
+  Req &r = S->reqs[ticket];
+  if (r.state != kQueued) return ht::set_error(HT_ERR_BUSY, "request already launched");
+  auto it = std::find(S->queue.begin(), S->queue.end(), ticket);
+  if (it != S->queue.end()) S->queue.erase(it);
+  r.state = kDone;
+  r.status = HT_ERR_ARG;
+  r.t_done = now_ns();
+  S->cv_done.notify_all();
+  return HT_OK;
+}
+
+int ht_server_stats(ht_server *S, ht_server_stats_t *out, int reset) {
+  if (!S || !out) return ht::set_error(HT_ERR_ARG, "ht_server_stats: bad arguments");
+  std::lock_guard<std::mutex> g(S->mu);
+  out->submitted = S->reqs.size();
+  out->completed = S->completed;
+  out->rejected = S->rejected;
+  out->batches = S->batches;
+  out->bytes_completed = S->bytes_completed;
+  out->p50_us = percentile(S->lat_us, 0.50);
+  out->p99_us = percentile(S->lat_us, 0.99);
+  double sum = 0, mx = 0;
+  for (double v : S->lat_us) {
+    sum += v;
+    mx = std::max(mx, v);
+  }
+  out->mean_us = S->lat_us.empty() ? 0.0 : sum / (double)S->lat_us.size();
+  out->max_us = mx;
+  out->wall_s = (S->last_done > S->first_arrive) ? (S->last_done - S->first_arrive) * 1e-9 : 0.0;
+  if (reset) {
+    S->lat_us.clear();
+    S->completed = 0;
+    S->bytes_completed = 0;
+    S->first_arrive = 0;
+    S->last_done = 0;
+  }
+  return HT_OK;
+}
+
+size_t ht_server_latencies(ht_server *S, double *out_us, size_t n) {
+  if (!S || !out_us) return 0;
+  std::lock_guard<std::mutex> g(S->mu);
+  const size_t m = std::min(n, S->lat_us.size());
+  std::copy(S->lat_us.begin(), S->lat_us.begin() + (ptrdiff_t)m, out_us);
+  return m;
+}
+
+int ht_server_destroy(ht_server *S) {
+  if (!S) return HT_OK;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->stop = true;
+  }
+  S->cv_dispatch.notify_all();
+  S->cv_complete.notify_all();
+  if (S->dispatcher.joinable()) S->dispatcher.join();
+  if (S->completer.joinable()) S->completer.join();
+  free_server(S);
+  return HT_OK;
+}
+
+}  // extern "C"

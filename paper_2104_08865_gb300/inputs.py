@@ -43,6 +43,49 @@ def splitmix64_words(seed: int, start: int, count: int) -> np.ndarray:
     return out
 
 
+def _u64_to_i64(v: int) -> int:
+    v &= 2**64 - 1
+    return v - 2**64 if v >= 2**63 else v
+
+
+def splitmix64_words_torch(seed: int, start: int, count: int, device):
+    """Same outputs as splitmix64_words, computed with torch int64 ops on
+    `device` (two's-complement wrap-around; logical shifts by masking)."""
+    import torch
+    out = torch.empty(count, dtype=torch.int64, device=device)
+    step = 1 << 26
+    g = _u64_to_i64(int(GAMMA))
+    m1 = _u64_to_i64(int(_M1))
+    m2 = _u64_to_i64(int(_M2))
+    s = _u64_to_i64(seed)
+
+    def lsr(z, n):
+        return (z >> n) & ((1 << (64 - n)) - 1)
+
+    for base in range(0, count, step):
+        n = min(step, count - base)
+        z = torch.arange(start + base + 1, start + base + 1 + n, dtype=torch.int64, device=device)
+        z.mul_(g).add_(s)
+        z.bitwise_xor_(lsr(z, 30)).mul_(m1)
+        z.bitwise_xor_(lsr(z, 27)).mul_(m2)
+        z.bitwise_xor_(lsr(z, 31))
+        out[base:base + n] = z
+    return out
+
+
+def stream_bytes_torch(seed: int, offset: int, length: int, device):
+    """stream_bytes as a uint8 torch tensor built on `device`."""
+    import torch
+    if length == 0:
+        return torch.zeros(0, dtype=torch.uint8, device=device)
+    w0 = offset // 8
+    w1 = (offset + length + 7) // 8
+    words = splitmix64_words_torch(seed, w0, w1 - w0, device)
+    raw = words.view(torch.uint8)  # little-endian hosts and GPUs
+    lo = offset - 8 * w0
+    return raw[lo:lo + length]
+
+
 def stream_bytes(seed: int, offset: int, length: int) -> np.ndarray:
     """Bytes [offset, offset+length) of the splitmix64 byte stream of `seed`."""
     if length == 0:

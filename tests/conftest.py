@@ -25,3 +25,23 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+_BUILT = False
+
+
+def ensure_built():
+    """Compile the oracle and the CUDA library (no-op when up to date)."""
+    global _BUILT
+    if not _BUILT:
+        import oracle
+        from paper_2104_08865_gb300 import build as _b
+        oracle.build()
+        _b.build()
+        _BUILT = True
+
+
+@pytest.fixture(scope="session")
+def built():
+    ensure_built()
+    return True

@@ -1,0 +1,199 @@
+"""GPU parity: every digest of the CUDA library, through the C ABI, equals the
+CPU oracle's bit for bit (integer arithmetic: the tolerance is zero).
+
+Inputs come from the seeded generators of paper_2104_08865_gb300.inputs; the
+oracle's seeds come from the oracle's own splitmix64, the library's from
+ht_seed_expand.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_08865_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WIDTHS = (16, 24, 32, 40)
+
+
+@pytest.fixture(scope="module")
+def dev(built):
+    torch.cuda.set_device(0)
+    return torch.device("cuda:0")
+
+
+def _pair(width, seed=7):
+    from paper_2104_08865_gb300 import Hasher, abi
+    ref = oracle.seed_expand(seed, oracle.seed_words(width))
+    lib = abi.ht_seed_expand(seed, width)
+    return Hasher(width, seed_words=lib), ref
+
+
+def _u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def _batch(h, dbuf, offs, lens, base_off=0):
+    ptrs = torch.tensor([dbuf.data_ptr() + base_off + int(o) for o in offs], dtype=torch.int64,
+                        device=dbuf.device)
+    ln = torch.tensor([int(n) for n in lens], dtype=torch.int64, device=dbuf.device)
+    out = h.hash_batch(ptrs, ln, len(lens))
+    h.status()
+    return _u64(out)
+
+
+def _singles(h, dbuf, offs, lens, base_off=0):
+    out = torch.empty((len(lens), h.k), dtype=torch.int64, device=dbuf.device)
+    for i, (o, n) in enumerate(zip(offs, lens)):
+        h.hash(dbuf, int(n), out=out[i], offset=base_off + int(o))
+    return _u64(out)
+
+
+def test_c1_hh16_1000_strings_of_4096(dev):
+    """1,000 strings of 4,096 random bytes (splitmix64 seed 1), HH16, seed 7."""
+    h, ref = _pair(16)
+    lens = [4096] * 1000
+    buf, offs = inputs.packed_batch(1, lens)
+    dbuf = torch.from_numpy(buf).to(dev)
+    want = oracle.hash_many(16, ref, buf, offs, lens)
+    assert np.array_equal(_batch(h, dbuf, offs, lens), want)
+    assert np.array_equal(_singles(h, dbuf, offs, lens), want)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_edge_sweep_all_lengths_and_contents(dev, width):
+    """Every length 0..8192 with zero, 0xFF, 8-byte-pattern and random content."""
+    h, ref = _pair(width)
+    lens, parts = [], []
+    for kind in ("zero", "ff", "pattern8", "random"):
+        for n in range(0, 8193):
+            lens.append(n)
+            parts.append(inputs.pattern_bytes(kind, n))
+    slots = [(n + 255) // 256 * 256 for n in lens]
+    offs = np.concatenate([[0], np.cumsum(slots)[:-1]]).astype(np.int64)
+    buf = np.zeros(int(sum(slots)) + 256, dtype=np.uint8)
+    for o, p in zip(offs, parts):
+        buf[o:o + len(p)] = p
+    want = oracle.hash_many(width, ref, buf, offs, lens)
+    dbuf = torch.from_numpy(buf).to(dev)
+    got = _batch(h, dbuf, offs, lens)
+    bad = np.nonzero(~np.all(got == want, axis=1))[0]
+    assert bad.size == 0, "first mismatches at lengths %s" % [lens[i] for i in bad[:10]]
+    sel = list(range(0, len(lens), 61))
+    got1 = _singles(h, dbuf, offs[sel], [lens[i] for i in sel])
+    assert np.array_equal(got1, want[sel])
+
+
+def _boundary_lengths(width):
+    xb = oracle.params(width)["exec_bytes"]
+    Ns = [1, 7, 8, 9, 63, 64, 65, 71, 72, 511, 512, 513, 575, 4095, 4096, 4097, 4096 + 512 + 64 + 9,
+          32767, 32768, 32769, 8 * 4096 + 3 * 512 + 5 * 64 + 7]
+    out = []
+    for i, N in enumerate(Ns):
+        out.append(N * xb)
+        out.append(N * xb + (i * 37) % xb)
+    return out
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("L", [2, 3])
+def test_chunk_and_tree_boundaries(dev, width, L):
+    """Execution counts around every f^l boundary (partial chunks, pending
+    roots at each level, complete upper groups) with ragged tails, for both
+    chunk heights."""
+    from paper_2104_08865_gb300 import abi
+    h, ref = _pair(width, seed=11)
+    for n in (0, 1 << 10, 1 << 16, 1 << 20, 1 << 24, 1 << 30, 2**64 - 1):
+        abi.ht_set_shape(h.ctx, n, L, 256, 32)
+    lens = _boundary_lengths(width)
+    buf, offs = inputs.packed_batch(21, lens)
+    want = oracle.hash_many(width, ref, buf, offs, lens)
+    dbuf = torch.from_numpy(buf).to(dev)
+    assert np.array_equal(_singles(h, dbuf, offs, lens), want)
+    assert np.array_equal(_batch(h, dbuf, offs, lens), want)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_unaligned_strings(dev, width):
+    """Strings starting at every byte offset 1..15 past a 16-byte boundary."""
+    h, ref = _pair(width, seed=3)
+    xb = oracle.params(width)["exec_bytes"]
+    lens = [5, xb - 1, xb + 3, 64 * xb + 11, 70 * xb + 100]
+    src = inputs.stream_bytes(9, 0, max(lens) + 64)
+    dbuf = torch.from_numpy(src).to(dev)
+    for sh in range(1, 16):
+        offs = [sh] * len(lens)
+        want = np.stack([oracle.hash_bytes(width, ref, src[sh:sh + n]) for n in lens])
+        assert np.array_equal(_singles(h, dbuf, offs, lens), want), sh
+        assert np.array_equal(_batch(h, dbuf, offs, lens), want), sh
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_c2_one_gib_string(dev, width):
+    """1 GiB of splitmix64(2) bytes, device-resident (the benchmark's input and
+    launch configuration), bit-exact against the oracle over the whole string;
+    the host-input path gives the same digest."""
+    h, ref = _pair(width)
+    n = 1 << 30
+    dbuf = inputs.stream_bytes_torch(2, 0, n, dev)
+    got = _u64(h.hash(dbuf))
+    host = dbuf.cpu().numpy()
+    want = oracle.hash_bytes(width, ref, host)
+    assert np.array_equal(got, want)
+    pinned = torch.empty(n, dtype=torch.uint8).pin_memory()
+    pinned.copy_(torch.from_numpy(host))
+    assert np.array_equal(h.hash_host(pinned.numpy()), want)
+
+
+def test_c4_batch_50000_log_uniform(dev):
+    """50,000 strings, lengths log-uniform in [64 B, 1 MiB] (splitmix64 seed 3),
+    HH24: the persistent batch launch, one launch per string and the oracle
+    agree on every digest."""
+    width = 24
+    h, ref = _pair(width)
+    lens = inputs.log_uniform_lengths(3, 50_000, 64, 1 << 20)
+    buf, offs = inputs.packed_batch(3, lens)
+    dbuf = torch.from_numpy(buf).to(dev)
+    got = _batch(h, dbuf, offs, lens)
+    naive = torch.empty((len(lens), 3), dtype=torch.int64, device=dev)
+    h.hash_batch_naive([dbuf.data_ptr() + int(o) for o in offs], lens, naive)
+    assert np.array_equal(_u64(naive), got)
+    want = oracle.hash_many(width, ref, buf, offs, lens)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("width", [24, 40])
+def test_autotuned_shape_keeps_digests(dev, width):
+    from paper_2104_08865_gb300 import abi
+    h, ref = _pair(width)
+    n = 48 << 20
+    best = abi.ht_autotune(h.ctx, n)
+    assert best["chunk_levels"] in (2, 3)
+    assert abi.ht_get_shape(h.ctx, n) == best
+    dbuf = inputs.stream_bytes_torch(5, 0, n + 333, dev)
+    want = oracle.hash_bytes(width, ref, dbuf.cpu().numpy())
+    assert np.array_equal(_u64(h.hash(dbuf)), want)
+
+
+def test_launch_counter_counts_kernels(dev):
+    h, _ = _pair(32)
+    dbuf = torch.zeros(1 << 20, dtype=torch.uint8, device=dev)
+    before = h.launches()
+    h.hash(dbuf)
+    ptrs = torch.tensor([dbuf.data_ptr()] * 3, dtype=torch.int64, device=dev)
+    ln = torch.tensor([10, 1000, 100000], dtype=torch.int64, device=dev)
+    h.hash_batch(ptrs, ln, 3)
+    torch.cuda.synchronize()
+    assert h.launches() - before == 3  # one hash kernel + planner + batch kernel
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_rekey_matches_fresh_context(dev, width):
+    from paper_2104_08865_gb300 import abi
+    h, _ = _pair(width, seed=1)
+    ref2 = oracle.seed_expand(99, oracle.seed_words(width))
+    abi.ht_ctx_rekey(h.ctx, abi.ht_seed_expand(99, width))
+    data = inputs.stream_bytes(6, 0, 3 * 64 * oracle.params(width)["exec_bytes"] + 5)
+    got = _u64(h.hash(torch.from_numpy(data).to(dev)))
+    assert np.array_equal(got, oracle.hash_bytes(width, ref2, data))

@@ -518,3 +518,16 @@ def test_collision_rate_diagnostic():
     assert full == 0
     expect = trials / 256.0
     assert abs(low - expect) < 5 * math.sqrt(expect)
+
+
+def test_torch_generator_matches_numpy():
+    """The device-side input generator (torch ops) reproduces the numpy one."""
+    torch = pytest.importorskip("torch")
+    for seed, start, count in [(2, 0, 1000), (3, 12345, 777), (2**64 - 1, 2**40, 64)]:
+        a = inputs.splitmix64_words(seed, start, count)
+        b = inputs.splitmix64_words_torch(seed, start, count, "cpu").numpy().view(np.uint64)
+        assert np.array_equal(a, b)
+    for off, n in [(0, 100), (3, 1000), (17, 1)]:
+        a = inputs.stream_bytes(4, off, n)
+        b = inputs.stream_bytes_torch(4, off, n, "cpu").numpy()
+        assert np.array_equal(a, b)
