@@ -1,0 +1,342 @@
+"""Benchmark: HalftimeHash throughput on GB300 (one JSON line on stdout).
+
+Default workload: one 1 GiB string of splitmix64(2) bytes, device-resident,
+hashed at each output width (16, 24, 32, 40 bytes) under seed 7.  One step =
+the four hashes (4 GiB hashed).  The input is larger than L2 (1 GiB vs
+129 MB), so no flush is needed between launches.
+
+  value   GB/s over the timed steps, CUDA events on the launching stream,
+          max over ranks (each rank hashes its own copy: weak scaling).
+  e2e     the same metric through ht_hash_host from pinned host memory: the
+          host-to-device copy of every step's input and the digest read-back
+          are inside the timed region.
+  roofline  the dominant kernel (the slowest width) against the measured HBM
+          copy bandwidth; algorithmic bytes = 2^30 read per launch.
+  cpu_baseline  the CPU oracle on the same bytes (one thread per width).
+
+`--impl reference` times the CPU oracle instead (the reference arm): each step
+hashes a bounded sample (the first 64 MiB of the string at each width).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WIDTHS = (16, 24, 32, 40)
+METRIC = "HalftimeHash GB/s hashed vs HBM roofline; served request p50/p99 latency"
+SEED_DATA = 2
+SEED_KEY = 7
+GIB = 1 << 30
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "25"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _oracle_gbs(data_np, n_bytes: int):
+    """The oracle over the first n_bytes at every width, one thread per width."""
+    import numpy as np
+
+    import oracle
+    sample = data_np[:n_bytes]
+    seeds = {w: oracle.seed_expand(SEED_KEY, oracle.seed_words(w)) for w in WIDTHS}
+    out = {}
+
+    def run(w):
+        out[w] = oracle.hash_bytes(w, seeds[w], sample)
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=run, args=(w,)) for w in WIDTHS]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    dt = time.perf_counter() - t0
+    return len(WIDTHS) * n_bytes / dt / 1e9, dt, out
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    from paper_2104_08865_gb300 import inputs
+    sample = 64 << 20
+    data = inputs.stream_bytes(SEED_DATA, 0, sample)
+    for _ in range(args.warmup):
+        _oracle_gbs(data, sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_gbs(data, sample)
+    dt = time.perf_counter() - t0
+    gbs = args.steps * len(WIDTHS) * sample / dt / 1e9
+    desc = ("first 64 MiB of the 1 GiB splitmix64(2) string at each of the four widths per step, "
+            "one oracle thread per width")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1000 * dt / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "1 GiB string, widths 16/24/32/40 (bounded sample: 64 MiB per width)"},
+        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": len(WIDTHS),
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2104_08865_gb300", "libhalftime.so")):
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_2104_08865_gb300 import Hasher, abi, inputs
+
+    nbytes = args.bytes
+    stream = torch.cuda.current_stream()
+    data = inputs.stream_bytes_torch(SEED_DATA, 0, nbytes, dev)
+    hashers = {w: Hasher(w, seed_words=abi.ht_seed_expand(SEED_KEY, w)) for w in WIDTHS}
+    shapes = {}
+    for w in WIDTHS:
+        if args.shape:
+            kern, L, st, tpb, bps = (int(v) for v in args.shape.split(","))
+            abi.ht_set_shape(hashers[w].ctx, nbytes, kern, L, st, tpb, bps)
+        elif not args.no_autotune:
+            abi.ht_autotune(hashers[w].ctx, nbytes, stream)
+        shapes[str(w)] = abi.ht_get_shape(hashers[w].ctx, nbytes)
+    outs = {w: torch.empty(w // 8, dtype=torch.int64, device=dev) for w in WIDTHS}
+
+    def step(evs=None):
+        for i, w in enumerate(WIDTHS):
+            if evs is not None:
+                evs[i][0].record(stream)
+            abi.ht_hash(hashers[w].ctx, data.data_ptr(), nbytes, outs[w].data_ptr(), stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches0 = sum(h.launches() for h in hashers.values())
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    per = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+            for _ in WIDTHS] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(per[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    launches = sum(h.launches() for h in hashers.values()) - launches0
+    ms_total = t_start.elapsed_time(t_end)
+    if ws > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    total_bytes = ws * args.steps * len(WIDTHS) * nbytes
+    value = total_bytes / (ms_total / 1e3) / 1e9
+    per_w = {}
+    for i, w in enumerate(WIDTHS):
+        ms = [per[s][i][0].elapsed_time(per[s][i][1]) for s in range(args.steps)]
+        per_w[w] = statistics.mean(ms)
+    dom = max(WIDTHS, key=lambda w: per_w[w])
+    peak, peak_kind = _peaks()
+    achieved = nbytes / (per_w[dom] / 1e3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath) and nbytes == GIB:
+        try:
+            traffic = json.load(open(tpath)).get(str(dom))
+        except Exception:
+            traffic = None
+    digests = {w: outs[w].cpu().numpy().view(np.uint64).tolist() for w in WIDTHS}
+
+    # ---- end to end: pinned host input through ht_hash_host ---------------
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        host.copy_(data)
+        hnp = host.numpy()
+        dig = np.zeros(5, dtype=np.uint64)
+        for w in WIDTHS:  # warm-up (staging ring allocation)
+            abi.ht_hash_host(hashers[w].ctx, hnp.ctypes.data, nbytes, dig.ctypes.data, stream)
+        torch.cuda.synchronize()
+        e_steps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            for w in WIDTHS:
+                abi.ht_hash_host(hashers[w].ctx, hnp.ctypes.data, nbytes, dig.ctypes.data, stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": round(ws * e_steps * len(WIDTHS) * nbytes / dt / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": len(WIDTHS) * nbytes,
+               "d2h_bytes_per_step": sum(w for w in WIDTHS), "steps": e_steps,
+               "path": "ht_hash_host: pinned host -> device in 64 MiB pieces overlapped with hashing"}
+        del host
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) --------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        host_np = data.cpu().numpy()
+        sample = min(nbytes, args.cpu_bytes)
+        gbs, dt, ref = _oracle_gbs(host_np, sample)
+        match = None
+        if sample == nbytes:
+            match = all(np.array_equal(np.asarray(digests[w], dtype=np.uint64), ref[w]) for w in WIDTHS)
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": len(WIDTHS), "kind": "oracle",
+               "sample": "first %d MiB of the string at each of the four widths, one oracle thread "
+                         "per width (%.1f s)" % (sample >> 20, dt),
+               "digests_match_gpu": match}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "one %d MiB string of splitmix64(%d) bytes, device-resident, hashed "
+                                   "at widths 16/24/32/40 (seed %d) per step" % (nbytes >> 20, SEED_DATA, SEED_KEY),
+                       "bytes_per_step": len(WIDTHS) * nbytes,
+                       "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "per_width_gbs": {str(w): round(nbytes / (per_w[w] / 1e3) / 1e9, 2) for w in WIDTHS},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": "%s<%d> (single string)" % (
+                             "stream_kernel" if shapes[str(dom)]["kernel"] == 0 else "hash_kernel", dom),
+                         "peak_source": peak_kind},
+            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": ck,
+            "shapes": shapes,
+            "digests": {str(w): ["%016x" % v for v in digests[w]] for w in WIDTHS},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--bytes", type=int, default=GIB, help="string size (profiling runs use less)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shape instead of autotuning it (setup, untimed)")
+    ap.add_argument("--shape", default="", help="force a launch shape kernel,chunk_levels,stages,threads_per_block,blocks_per_sm")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-bytes", type=int, default=GIB)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and args.steps > 2:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

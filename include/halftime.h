@@ -90,7 +90,7 @@ int ht_ctx_rekey(ht_ctx *ctx, const uint64_t *seed_words_host, size_t n_words,
 
 /* Reserves device scratch so that ht_hash_batch can take up to max_strings
  * strings whose lengths add up to at most max_total_bytes (the default after
- * ht_ctx_create is 65536 strings and 64 GiB).  Synchronises the device.
+ * ht_ctx_create is 65536 strings and 16 GiB).  Synchronises the device.
  * Errors: HT_ERR_ARG, HT_ERR_NOMEM, HT_ERR_CUDA. */
 int ht_ctx_reserve(ht_ctx *ctx, uint64_t max_total_bytes, size_t max_strings);
 
@@ -147,13 +147,23 @@ int ht_hash_batch_naive(ht_ctx *ctx, const void *const *ptrs_host,
                         uint64_t *digests_dev, ht_stream_t stream);
 
 /* ---- launch shapes and autotuning ------------------------------------------
- * A launch shape is (chunk height L: a warp hashes 8^L executions before
- * handing its tree root to the cross-warp levels; threads per block; blocks
- * per SM).  The context caches one shape per length bucket
- * (bucket = floor(log2(len)), 0..63) and one for batches. */
+ * Three kernel families compute the same digests:
+ *   kernel 0, the stream kernel: every warp owns a ring of `stages`
+ *     shared-memory slots, each filled with one bulk copy (TMA) of 8
+ *     executions, and hashes an equal, contiguous share of the work;
+ *   kernel 1, the warp-chunk kernel (default): warps take chunks of 8^L
+ *     executions from an atomic cursor and load them with 128-bit loads;
+ *   kernel 2, the hybrid kernel: like kernel 1 with 64-execution chunks, but
+ *     the last stretch of the launch is handed out as single 8-execution
+ *     units.
+ * A shape also fixes the threads per block and blocks per SM.  The context
+ * caches one shape per length bucket (bucket = floor(log2(len)), 0..63) and
+ * one for batches. */
 typedef struct ht_shape {
-  int chunk_levels;      /* L: 2 or 3 */
-  int threads_per_block; /* 64 .. 1024, multiple of 32 */
+  int kernel;            /* 0: stream, 1: warp-chunk, 2: hybrid kernel */
+  int chunk_levels;      /* warp-chunk kernel: L = 1, 2 or 3 */
+  int stages;            /* stream kernel: shared-memory stages per warp, 2..8 */
+  int threads_per_block; /* multiple of 32, at most 256 */
   int blocks_per_sm;     /* 1 .. 32; clamped to the occupancy limit */
 } ht_shape;
 

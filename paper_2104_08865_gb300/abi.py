@@ -42,8 +42,8 @@ class HalftimeError(RuntimeError):
 
 
 class ht_shape(ctypes.Structure):
-    _fields_ = [("chunk_levels", ctypes.c_int), ("threads_per_block", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int)]
+    _fields_ = [("kernel", ctypes.c_int), ("chunk_levels", ctypes.c_int), ("stages", ctypes.c_int),
+                ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
 
 
 class ht_server_opts(ctypes.Structure):
@@ -224,9 +224,9 @@ def ht_get_shape(ctx: int, length: int) -> dict:
     return {n: getattr(s, n) for n, _ in ht_shape._fields_}
 
 
-def ht_set_shape(ctx: int, length: int, chunk_levels: int, threads_per_block: int,
-                 blocks_per_sm: int) -> None:
-    s = ht_shape(chunk_levels, threads_per_block, blocks_per_sm)
+def ht_set_shape(ctx: int, length: int, kernel: int = 0, chunk_levels: int = 2, stages: int = 3,
+                 threads_per_block: int = 192, blocks_per_sm: int = 1) -> None:
+    s = ht_shape(kernel, chunk_levels, stages, threads_per_block, blocks_per_sm)
     _check(_lib.ht_set_shape(ctx, length, ctypes.byref(s)))
 
 

@@ -74,6 +74,11 @@ uint64_t groups_of(uint64_t N, int L) {
   return g;
 }
 
+// Tree-group slots any batch of `total_exec` executions can need at any chunk
+// height: sum over strings of groups_of(N_i, 1) <= total_exec * (1/64 + 1/512
+// + ...) < total_exec / 56.
+static uint64_t groups_bound(uint64_t total_exec) { return total_exec / 56 + 1024; }
+
 static int bucket_of(uint64_t len) {
   if (len == UINT64_MAX) return 64;
   int b = 0;
@@ -93,6 +98,10 @@ static void free_scratch(ht_ctx *c) {
   cudaFree(c->str_done);
   cudaFree(c->plans);
   cudaFree(c->item0s);
+  cudaFree(c->chunk0s);
+  cudaFree(c->unitb0s);
+  c->chunk0s = nullptr;
+  c->unitb0s = nullptr;
   c->grp_acc = nullptr;
   c->grp_cnt = nullptr;
   c->str_acc = nullptr;
@@ -118,6 +127,8 @@ static int alloc_scratch(ht_ctx *c, uint64_t groups, uint64_t strings) {
   grab((void **)&c->str_done, strings * sizeof(unsigned int));
   grab((void **)&c->plans, strings * sizeof(StrPlan));
   grab((void **)&c->item0s, (strings + 1) * sizeof(unsigned long long));
+  grab((void **)&c->chunk0s, (strings + 1) * sizeof(unsigned long long));
+  grab((void **)&c->unitb0s, (strings + 1) * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     free_scratch(c);
     return cuda_error(e, "scratch allocation");
@@ -160,55 +171,95 @@ static void fill_keys(const ht_ctx *c, KParams &P) {
   P.scr = scratch_view(c);
 }
 
-// Blocks per SM a kernel reaches with tpb threads (at least 1).
-static int occupancy(const void *func, int tpb) {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, tpb, 0) != cudaSuccess) n = 1;
-  return std::max(n, 1);
+// Dynamic shared memory of a stream-kernel block: per warp, `stages` slots of
+// 8 executions plus one 8-byte mbarrier per slot, rounded to 128 bytes.
+static size_t stream_smem(const KernelSet &ks, const ht_shape &s) {
+  const size_t slot = 8 * (size_t)ks.exec_bytes;
+  const size_t per_warp = ((size_t)s.stages * (slot + 8) + 127) & ~(size_t)127;
+  return per_warp * (size_t)(s.threads_per_block / 32);
 }
 
+// Blocks per SM a kernel reaches (0 if it cannot run at all).
+static int occupancy(const void *func, int tpb, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, tpb, smem) != cudaSuccess) n = 0;
+  return n;
+}
+
+// The warp-chunk kernel with 64-execution chunks measured fastest on GB300
+// for long strings (the autotuner confirms or overrides per length bucket).
 static ht_shape default_shape() {
   ht_shape s;
+  s.kernel = 1;
   s.chunk_levels = 2;
+  s.stages = 3;
   s.threads_per_block = 256;
-  s.blocks_per_sm = 32;  // clamped to occupancy at launch
+  s.blocks_per_sm = 2;
   return s;
 }
 
 static bool shape_ok(const ht_shape &s) {
-  return (s.chunk_levels == 2 || s.chunk_levels == 3) && s.threads_per_block >= 32 &&
-         s.threads_per_block <= 256 && s.threads_per_block % 32 == 0 && s.blocks_per_sm >= 1 &&
-         s.blocks_per_sm <= 32;
+  if (s.threads_per_block < 32 || s.threads_per_block % 32 != 0 || s.blocks_per_sm < 1 ||
+      s.blocks_per_sm > 32)
+    return false;
+  if (s.kernel == 0) return s.stages >= 2 && s.stages <= 8 && s.threads_per_block <= 256;
+  if (s.kernel == 1)
+    return s.chunk_levels >= 1 && s.chunk_levels <= 3 && s.threads_per_block <= 256;
+  return s.kernel == 2 && s.threads_per_block <= 256;
+}
+
+// Work units of a string for a shape: stream/range units (8 executions each,
+// plus the tail unit) or warp-chunk items (8^L executions each, at least one).
+static uint64_t units_for(const ht_shape &s, uint64_t N) {
+  return s.kernel != 1 ? ((N + 7) >> 3) + 1 : items_of(N, s.chunk_levels);
+}
+static uint64_t unit_bytes(const KernelSet &ks, const ht_shape &s) {
+  return (uint64_t)ks.exec_bytes << (s.kernel != 1 ? 3 : 3 * s.chunk_levels);
+}
+static uint64_t groups_for(const ht_shape &s, uint64_t N) {
+  return groups_of(N, s.kernel != 1 ? 1 : s.chunk_levels);
 }
 
 // ---- single-string launch -------------------------------------------------------
 
-// Launches the single-string kernel over items [item_begin, item_end) of the
-// string described by sp.  digest_dev receives k words when the string's last
-// item completes.
-int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp,
-                  uint64_t item_begin, uint64_t item_end, uint64_t *digest_dev,
-                  cudaStream_t s) {
+// Launches one kernel over units [u_begin, u_end) of the string described by
+// sp (sp.n_items = all units of the string).  digest_dev receives k words
+// when the string's last unit completes.
+int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t u_begin,
+                  uint64_t u_end, uint64_t *digest_dev, cudaStream_t s) {
   const KernelSet &ks = *c->ks;
-  const int L = shape.chunk_levels;
-  const bool aligned = (((uintptr_t)sp.ptr) & 15u) == 0;
-  const void *func = aligned ? ks.single_aligned[L - 2] : ks.single_unaligned[L - 2];
+  const void *func;
+  size_t smem = 0;
+  if (shape.kernel == 0) {
+    func = ks.stream_single;
+    smem = stream_smem(ks, shape);
+  } else if (shape.kernel == 2) {
+    func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.range_single : ks.range_single_unaligned;
+  } else {
+    const int L = shape.chunk_levels;
+    func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.single_aligned[L - 1] : ks.single_unaligned[L - 1];
+  }
   const int tpb = shape.threads_per_block;
-  const int bps = std::min(shape.blocks_per_sm, occupancy(func, tpb));
-  const uint64_t warps_needed = item_end - item_begin;
+  const int occ = occupancy(func, tpb, smem);
+  if (occ == 0) return set_error(HT_ERR_ARG, "launch shape does not fit the device");
+  const int bps = std::min(shape.blocks_per_sm, occ);
   const uint64_t wpb = (uint64_t)tpb / 32;
-  uint64_t grid = std::min<uint64_t>((uint64_t)c->num_sms * bps, (warps_needed + wpb - 1) / wpb);
+  // stream/range: a few units per warp at least; warp-chunk: one item per warp
+  const uint64_t per_warp = shape.kernel != 1 ? 4 : 1;
+  const uint64_t want = (u_end - u_begin + per_warp * wpb - 1) / (per_warp * wpb);
+  uint64_t grid = std::min<uint64_t>((uint64_t)c->num_sms * bps, want);
   grid = std::max<uint64_t>(grid, 1);
   KParams P;
   fill_keys(c, P);
   P.single = sp;
-  P.item_begin = item_begin;
-  P.item_end = item_end;
+  P.item_begin = u_begin;
+  P.item_end = u_end;
   P.digests = (unsigned long long *)digest_dev;
   P.count = 1;
   P.total_warps = (unsigned)(grid * wpb);
+  P.stages = (unsigned)shape.stages;
   void *args[] = {&P};
-  HT_CUDA(cudaLaunchKernel(func, dim3((unsigned)grid), dim3(tpb), args, 0, s));
+  HT_CUDA(cudaLaunchKernel(func, dim3((unsigned)grid), dim3(tpb), args, smem, s));
   c->launches.fetch_add(1);
   return HT_OK;
 }
@@ -267,14 +318,20 @@ int ht_ctx_create(int width, const uint64_t *seed_words, size_t n_words, ht_stre
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), s);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_digest, 8 * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ks->stream_single, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ks->stream_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  c->smem_optin = optin;
   if (e != cudaSuccess) {
     int rc = cuda_error(e, "ht_ctx_create");
     ht_ctx_destroy(c);
     return rc;
   }
-  // default reserve: 64 GiB over at most 65536 strings
-  const uint64_t total_exec = (64ull << 30) / (uint64_t)ks->exec_bytes;
-  int rc = alloc_scratch(c, total_exec / 448 + 1024, 65536);
+  // default reserve: 16 GiB over at most 65536 strings
+  int rc = alloc_scratch(c, groups_bound((16ull << 30) / (uint64_t)ks->exec_bytes), 65536);
   if (rc != HT_OK) {
     ht_ctx_destroy(c);
     return rc;
@@ -317,10 +374,9 @@ int ht_ctx_rekey(ht_ctx *c, const uint64_t *seed_words, size_t n_words, ht_strea
 int ht_ctx_reserve(ht_ctx *c, uint64_t max_total_bytes, size_t max_strings) {
   if (!c || max_strings == 0) return set_error(HT_ERR_ARG, "ht_ctx_reserve: bad arguments");
   HT_CUDA(cudaDeviceSynchronize());
-  const uint64_t total_exec = max_total_bytes / (uint64_t)c->ks->exec_bytes;
   free_scratch(c);
   c->graph_valid = false;
-  return alloc_scratch(c, total_exec / 448 + 1024, max_strings);
+  return alloc_scratch(c, groups_bound(max_total_bytes / (uint64_t)c->ks->exec_bytes), max_strings);
 }
 
 int ht_ctx_status(ht_ctx *c, ht_stream_t stream) {
@@ -331,7 +387,9 @@ int ht_ctx_status(ht_ctx *c, ht_stream_t stream) {
   if (st) {
     unsigned int zero = 0;
     HT_CUDA(cudaMemcpy(&c->ctl->status, &zero, sizeof zero, cudaMemcpyHostToDevice));
-    return set_error(HT_ERR_TOO_LONG, "a batch exceeded the reserved scratch (no digests written)");
+    if (st & kStatusTooLong)
+      return set_error(HT_ERR_TOO_LONG, "a batch exceeded the reserved scratch (no digests written)");
+    return set_error(HT_ERR_DEVICE, "a kernel gave up waiting for a shared-memory stage (status %u)", st);
   }
   return HT_OK;
 }
@@ -340,20 +398,19 @@ int ht_hash(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest, ht_stre
   if (!c || !digest || (len && !data)) return set_error(HT_ERR_ARG, "ht_hash: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   const ht_shape shape = c->shapes[bucket_of(len)];
-  const int L = shape.chunk_levels;
   StrPlan sp;
   sp.ptr = (const uint8_t *)data;
   sp.len = len;
   sp.n_exec = len / (uint64_t)c->ks->exec_bytes;
   sp.item0 = 0;
   sp.grp0 = 0;
-  const uint64_t n_items = items_of(sp.n_exec, L);
-  if (n_items > 0xffffffffull) return set_error(HT_ERR_TOO_LONG, "string too long for one launch");
-  sp.n_items = (uint32_t)n_items;
+  const uint64_t n_units = units_for(shape, sp.n_exec);
+  if (n_units > 0xffffffffull) return set_error(HT_ERR_TOO_LONG, "string too long for one launch");
+  sp.n_items = (uint32_t)n_units;
   sp.pad = 0;
-  int rc = ensure_groups(c, groups_of(sp.n_exec, L), s);
+  int rc = ensure_groups(c, groups_for(shape, sp.n_exec), s);
   if (rc) return rc;
-  return launch_single(c, shape, sp, 0, n_items, digest, s);
+  return launch_single(c, shape, sp, 0, n_units, digest, s);
 }
 
 int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_host,
@@ -362,12 +419,13 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
   cudaStream_t s = (cudaStream_t)stream;
   const KernelSet &ks = *c->ks;
   const ht_shape shape = c->shapes[bucket_of(len)];
-  const int L = shape.chunk_levels;
   const uint64_t B = (uint64_t)ks.exec_bytes;
-  const uint64_t chunk_bytes = B << (3 * L);
-  // pieces of whole chunks, about 64 MiB each; a slot also holds the tail
-  const uint64_t items_per_piece = std::max<uint64_t>(1, (64ull << 20) / chunk_bytes);
-  const uint64_t slot_bytes = ((items_per_piece * chunk_bytes + B + 255) / 256) * 256;
+  const uint64_t ub = unit_bytes(ks, shape);
+  // pieces of whole units, about 64 MiB each (whole 64-execution chunks for
+  // the unit-based kernels); a slot also holds the tail
+  uint64_t units_per_piece = std::max<uint64_t>(1, (64ull << 20) / ub);
+  if (shape.kernel != 1) units_per_piece = std::max<uint64_t>(8, units_per_piece & ~7ull);
+  const uint64_t slot_bytes = ((units_per_piece * ub + B + 255) / 256) * 256;
   if (!c->copy_stream) HT_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
   if (c->stage_bytes < slot_bytes) {
     HT_CUDA(cudaDeviceSynchronize());
@@ -387,20 +445,22 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
   sp.n_exec = len / B;
   sp.item0 = 0;
   sp.grp0 = 0;
-  const uint64_t n_items = items_of(sp.n_exec, L);
-  if (n_items > 0xffffffffull) return set_error(HT_ERR_TOO_LONG, "string too long for one launch");
-  sp.n_items = (uint32_t)n_items;
+  const uint64_t n_units = units_for(shape, sp.n_exec);
+  if (n_units > 0xffffffffull) return set_error(HT_ERR_TOO_LONG, "string too long for one launch");
+  sp.n_items = (uint32_t)n_units;
   sp.pad = 0;
-  int rc = ensure_groups(c, groups_of(sp.n_exec, L), s);
+  int rc = ensure_groups(c, groups_for(shape, sp.n_exec), s);
   if (rc) return rc;
   // slots may still be read by an earlier call's kernels on another stream
   HT_CUDA(cudaStreamSynchronize(s));
   const uint8_t *host = (const uint8_t *)data;
+  const uint64_t data_end = sp.n_exec * B;  // bytes read by EHC
   uint64_t piece = 0;
-  for (uint64_t it0 = 0; it0 < n_items; it0 += items_per_piece, ++piece) {
-    const uint64_t it1 = std::min(n_items, it0 + items_per_piece);
-    const uint64_t b0 = it0 * chunk_bytes;
-    const uint64_t b1 = (it1 == n_items) ? len : it1 * chunk_bytes;
+  for (uint64_t u0 = 0; u0 < n_units; u0 += units_per_piece, ++piece) {
+    const uint64_t u1 = std::min(n_units, u0 + units_per_piece);
+    // bytes of units [u0, u1); the last piece also carries the tail
+    const uint64_t b0 = std::min(u0 * ub, data_end);
+    const uint64_t b1 = (u1 == n_units) ? len : std::min(u1 * ub, data_end);
     const int slot = (int)(piece % kStageSlots);
     if (piece >= (uint64_t)kStageSlots) HT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_hash[slot], 0));
     if (b1 > b0)
@@ -410,7 +470,7 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
     // the kernel addresses the string from its start; shift the base so
     // that byte b0 lands at the slot
     sp.ptr = c->stage[slot] - b0;
-    rc = launch_single(c, shape, sp, it0, it1, c->d_digest, s);
+    rc = launch_single(c, shape, sp, u0, u1, c->d_digest, s);
     if (rc) return rc;
     HT_CUDA(cudaEventRecord(c->ev_hash[slot], s));
   }
@@ -419,34 +479,61 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
   return HT_OK;
 }
 
+// The batch graph: planner node -> hash node.  Node parameters are replaced
+// on every call; the graph is rebuilt when the batch shape changes.
+static void batch_nodes(ht_ctx *c, const ht_shape &shape, cudaKernelNodeParams &np,
+                        cudaKernelNodeParams &nh, void **pargs, void **hargs) {
+  const KernelSet &ks = *c->ks;
+  np = {};
+  np.func = (void *)ks.plan[shape.kernel != 1 ? 0 : shape.chunk_levels];
+  np.gridDim = dim3(1);
+  np.blockDim = dim3(1024);
+  pargs[0] = &c->plan_args;
+  np.kernelParams = pargs;
+  nh = {};
+  size_t smem = 0;
+  const void *func;
+  if (shape.kernel == 0) {
+    func = ks.stream_batch;
+    smem = stream_smem(ks, shape);
+  } else if (shape.kernel == 2) {
+    func = ks.range_batch;
+  } else {
+    func = ks.batch[shape.chunk_levels - 1];
+  }
+  const int tpb = shape.threads_per_block;
+  const int bps = std::max(1, std::min(shape.blocks_per_sm, occupancy(func, tpb, smem)));
+  nh.func = (void *)func;
+  nh.gridDim = dim3((unsigned)(c->num_sms * bps));
+  nh.blockDim = dim3(tpb);
+  nh.sharedMemBytes = (unsigned)smem;
+  c->batch_params.total_warps = (unsigned)(c->num_sms * bps * (tpb / 32));
+  c->batch_params.stages = (unsigned)shape.stages;
+  c->plan_args.total_warps = c->batch_params.total_warps;
+  hargs[0] = &c->batch_params;
+  nh.kernelParams = hargs;
+}
+
 static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
   c->graph = nullptr;
-  const KernelSet &ks = *c->ks;
-  const int L = shape.chunk_levels;
+  c->node_hash2 = nullptr;
+  cudaKernelNodeParams np, nh;
+  void *pargs[1], *hargs[1];
+  batch_nodes(c, shape, np, nh, pargs, hargs);
   HT_CUDA(cudaGraphCreate(&c->graph, 0));
-  cudaKernelNodeParams np = {};
-  np.func = (void *)ks.plan[L - 2];
-  np.gridDim = dim3(1);
-  np.blockDim = dim3(1024);
-  void *pargs[] = {&c->plan_args};
-  np.kernelParams = pargs;
   HT_CUDA(cudaGraphAddKernelNode(&c->node_plan, c->graph, nullptr, 0, &np));
-  cudaKernelNodeParams nh = {};
-  const void *func = ks.batch[L - 2];
-  const int tpb = shape.threads_per_block;
-  const int bps = std::min(shape.blocks_per_sm, occupancy(func, tpb));
-  nh.func = (void *)func;
-  nh.gridDim = dim3((unsigned)(c->num_sms * bps));
-  nh.blockDim = dim3(tpb);
-  c->batch_params.total_warps = (unsigned)(c->num_sms * bps * (tpb / 32));
-  void *hargs[] = {&c->batch_params};
-  nh.kernelParams = hargs;
   HT_CUDA(cudaGraphAddKernelNode(&c->node_hash, c->graph, &c->node_plan, 1, &nh));
+  if (shape.kernel == 2) {
+    // the general (unaligned-capable) variant; the one the planner's flag
+    // does not select returns at once
+    cudaKernelNodeParams nu = nh;
+    nu.func = (void *)c->ks->range_batch_unaligned;
+    HT_CUDA(cudaGraphAddKernelNode(&c->node_hash2, c->graph, &c->node_hash, 1, &nu));
+  }
   HT_CUDA(cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
-  c->node_hash_params = nh;
   c->graph_shape = shape;
   c->graph_valid = true;
   return HT_OK;
@@ -462,43 +549,41 @@ int ht_hash_batch(ht_ctx *c, const void *const *ptrs, const uint64_t *lens, size
                      (unsigned long long)c->cap_strings);
   cudaStream_t s = (cudaStream_t)stream;
   const ht_shape shape = c->shapes[64];
-  const KernelSet &ks = *c->ks;
   PlanArgs &A = c->plan_args;
   A.ptrs = ptrs;
   A.lens = lens;
   A.count = (unsigned)count;
   A.plans = c->plans;
   A.item0s = c->item0s;
+  A.chunk0s = c->chunk0s;
+  A.unitb0s = c->unitb0s;
   A.ctl = c->ctl;
   A.cap_groups = c->cap_groups;
   KParams &P = c->batch_params;
   fill_keys(c, P);
   P.plans = c->plans;
   P.item0s = c->item0s;
+  P.chunk0s = c->chunk0s;
+  P.unitb0s = c->unitb0s;
   P.digests = (unsigned long long *)digests;
   P.count = (unsigned)count;
-  const int L = shape.chunk_levels;
-  const void *func = ks.batch[L - 2];
-  const int bps = std::min(shape.blocks_per_sm, occupancy(func, shape.threads_per_block));
-  P.total_warps = (unsigned)(c->num_sms * bps * (shape.threads_per_block / 32));
   if (!c->graph_valid || memcmp(&c->graph_shape, &shape, sizeof shape) != 0) {
     int rc = build_batch_graph(c, shape);
     if (rc) return rc;
   } else {
-    cudaKernelNodeParams np = {};
-    np.func = (void *)ks.plan[L - 2];
-    np.gridDim = dim3(1);
-    np.blockDim = dim3(1024);
-    void *pargs[] = {&c->plan_args};
-    np.kernelParams = pargs;
+    cudaKernelNodeParams np, nh;
+    void *pargs[1], *hargs[1];
+    batch_nodes(c, shape, np, nh, pargs, hargs);
     HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_plan, &np));
-    cudaKernelNodeParams nh = c->node_hash_params;
-    void *hargs[] = {&c->batch_params};
-    nh.kernelParams = hargs;
     HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash, &nh));
+    if (c->node_hash2) {
+      cudaKernelNodeParams nu = nh;
+      nu.func = (void *)c->ks->range_batch_unaligned;
+      HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash2, &nu));
+    }
   }
   HT_CUDA(cudaGraphLaunch(c->graph_exec, s));
-  c->launches.fetch_add(2);
+  c->launches.fetch_add(c->node_hash2 ? 3 : 2);
   return HT_OK;
 }
 
@@ -531,6 +616,42 @@ uint64_t ht_ctx_launches(ht_ctx *c) { return c ? c->launches.load() : 0; }
 int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
   if (!c || len == UINT64_MAX) return set_error(HT_ERR_ARG, "ht_autotune: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
+  const KernelSet &ks = *c->ks;
+  // candidate shapes of both kernel families that fit the device
+  std::vector<ht_shape> cands;
+  for (int warps : {2, 3, 4, 5, 6, 8})
+    for (int stages : {2, 3, 4, 6})
+      for (int bps : {1, 2, 3, 4}) {
+        ht_shape h = default_shape();
+        h.kernel = 0;
+        h.stages = stages;
+        h.threads_per_block = 32 * warps;
+        h.blocks_per_sm = bps;
+        const size_t smem = stream_smem(ks, h);
+        if ((int)smem > c->smem_optin) continue;
+        if (occupancy(ks.stream_single, h.threads_per_block, smem) < bps) continue;
+        cands.push_back(h);
+      }
+  for (int tpb : {128, 256})
+    for (int bps : {1, 2, 3, 4, 6, 8}) {
+      ht_shape h = default_shape();
+      h.kernel = 2;
+      h.threads_per_block = tpb;
+      h.blocks_per_sm = bps;
+      if (occupancy(ks.range_single, tpb, 0) < bps) continue;
+      cands.push_back(h);
+    }
+  for (int L : {2, 3})
+    for (int tpb : {128, 256})
+      for (int bps : {1, 2, 3, 4, 6, 8}) {
+        ht_shape h = default_shape();
+        h.kernel = 1;
+        h.chunk_levels = L;
+        h.threads_per_block = tpb;
+        h.blocks_per_sm = bps;
+        if (occupancy(ks.single_aligned[L - 1], tpb, 0) < bps) continue;
+        cands.push_back(h);
+      }
   uint8_t *buf = nullptr;
   HT_CUDA(cudaMalloc((void **)&buf, std::max<uint64_t>(len, 16)));
   cudaEvent_t e0, e1;
@@ -539,41 +660,34 @@ int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
   int rc = HT_OK;
   cudaError_t ce = cudaMemsetAsync(buf, 0x5A, std::max<uint64_t>(len, 16), s);
   if (ce != cudaSuccess) rc = cuda_error(ce, "cudaMemsetAsync");
-  const ht_shape saved = c->shapes[bucket_of(len)];
+  const int bk = bucket_of(len);
+  const ht_shape saved = c->shapes[bk];
   ht_shape winner = saved;
   float best_ms = 1e30f;
-  const int Ls[2] = {2, 3};
-  const int tpbs[2] = {128, 256};
-  const int bpss[6] = {1, 2, 3, 4, 6, 8};
-  for (int li = 0; li < 2 && rc == HT_OK; ++li)
-    for (int ti = 0; ti < 2 && rc == HT_OK; ++ti)
-      for (int bi = 0; bi < 6 && rc == HT_OK; ++bi) {
-        ht_shape cand;
-        cand.chunk_levels = Ls[li];
-        cand.threads_per_block = tpbs[ti];
-        cand.blocks_per_sm = bpss[bi];
-        const void *func = c->ks->single_aligned[cand.chunk_levels - 2];
-        if (cand.blocks_per_sm > occupancy(func, cand.threads_per_block)) continue;
-        c->shapes[bucket_of(len)] = cand;
-        rc = ht_hash(c, buf, len, c->d_digest, stream);  // warm-up
-        if (rc) break;
-        float times[3];
-        for (int r = 0; r < 3 && rc == HT_OK; ++r) {
-          cudaEventRecord(e0, s);
-          rc = ht_hash(c, buf, len, c->d_digest, stream);
-          cudaEventRecord(e1, s);
-          cudaEventSynchronize(e1);
-          cudaEventElapsedTime(&times[r], e0, e1);
-        }
-        if (rc) break;
-        std::sort(times, times + 3);
-        if (times[1] < best_ms) {
-          best_ms = times[1];
-          winner = cand;
-        }
-      }
-  c->shapes[bucket_of(len)] = (rc == HT_OK) ? winner : saved;
+  for (size_t i = 0; i < cands.size() && rc == HT_OK; ++i) {
+    c->shapes[bk] = cands[i];
+    rc = ht_hash(c, buf, len, c->d_digest, stream);  // warm-up
+    float times[3] = {0, 0, 0};
+    for (int r = 0; r < 3 && rc == HT_OK; ++r) {
+      cudaEventRecord(e0, s);
+      rc = ht_hash(c, buf, len, c->d_digest, stream);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&times[r], e0, e1);
+    }
+    if (rc) break;
+    std::sort(times, times + 3);
+    if (times[1] < best_ms) {
+      best_ms = times[1];
+      winner = cands[i];
+    }
+  }
+  c->shapes[bk] = (rc == HT_OK) ? winner : saved;
   cudaStreamSynchronize(s);
+  if (rc == HT_OK) {
+    int st = ht_ctx_status(c, stream);
+    if (st) rc = st;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);

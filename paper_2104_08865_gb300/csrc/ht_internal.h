@@ -15,8 +15,14 @@ struct StrPlan {
   uint64_t n_exec;     // N = floor(len / exec_bytes): EHC executions
   uint64_t item0;      // first global work item of this string
   uint64_t grp0;       // first tree-group slot of this string in scratch
-  uint32_t n_items;    // work items: max(1, ceil(N / 8^L))
+  uint32_t n_items;    // work items: max(1, ceil(N / 8^L)), or stream/range units
   uint32_t pad;
+  // hybrid kernel work list (planner): full 64-execution chunks before this
+  // string in the batch, full chunks of this string taken whole in phase A,
+  // and phase-B units before this string
+  uint64_t chunk0;
+  uint64_t chunks_a;
+  uint64_t unitb0;
 };
 
 // Launch-wide control words (one per context).  cursor and exit return to 0
@@ -25,10 +31,15 @@ struct Ctl {
   unsigned long long cursor;  // next work item to hand out
   unsigned long long total;   // work items of the current batch (planner)
   unsigned long long groups;  // tree-group slots the batch needs (planner)
+  unsigned long long chunks_a;  // hybrid kernel: phase-A work items (whole chunks)
+  unsigned long long units_b;   // hybrid kernel: phase-B work items (single units)
   unsigned int exit;          // warps that have left the work loop
   unsigned int status;        // 0 or kStatusTooLong
+  unsigned int unaligned;     // planner: some string of the batch is not 16-byte aligned
+  unsigned int pad;
 };
-constexpr unsigned int kStatusTooLong = 1;
+constexpr unsigned int kStatusTooLong = 1;  // a batch exceeded the scratch
+// (kStatusTimeout = 2: a bounded wait on a stage's mbarrier ran out)
 
 // Device scratch of one context.
 struct Scratch {
@@ -49,11 +60,14 @@ struct KParams {
   Scratch scr;
   const StrPlan *plans;         // batch mode: planner output
   const unsigned long long *item0s;  // batch mode: item0 of each string (+ total)
+  const unsigned long long *chunk0s;  // batch mode: chunk0 of each string (+ total)
+  const unsigned long long *unitb0s;  // batch mode: unitb0 of each string (+ total)
   unsigned long long *digests;  // count * k words
   StrPlan single;               // single-string mode: the string
   unsigned long long item_begin, item_end;  // single mode: item range of this launch
   unsigned int count;           // batch mode: strings
-  unsigned int total_warps;     // warps in the grid (exit protocol)
+  unsigned int total_warps;     // warps in the grid
+  unsigned int stages;          // stream kernel: shared-memory slots per warp
 };
 
 struct PlanArgs {
@@ -62,17 +76,28 @@ struct PlanArgs {
   unsigned int count;
   StrPlan *plans;
   unsigned long long *item0s;
+  unsigned long long *chunk0s;
+  unsigned long long *unitb0s;
   Ctl *ctl;
   uint64_t cap_groups;
+  unsigned int total_warps;  // warps of the hash kernel (hybrid work list)
 };
 
-// Kernel variants of one width: chunk height L in {2, 3}; single-string or
-// batch; batch kernels also carry the unaligned-load path.
+// Kernel variants of one width.  Warp-chunk kernels: chunk height L in
+// {1, 2, 3}; single-string or batch; batch kernels also carry the
+// unaligned-load path.  Stream kernels (TMA stages): single-string or batch.
+// Planners: [0] stream units, [L] warp-chunk items of height L.
 struct KernelSet {
-  const void *single_aligned[2];    // [L-2]
-  const void *single_unaligned[2];  // [L-2]
-  const void *batch[2];             // [L-2]
-  const void *plan[2];              // [L-2]
+  const void *single_aligned[3];    // [L-1]
+  const void *single_unaligned[3];  // [L-1]
+  const void *batch[3];             // [L-1]
+  const void *plan[4];              // [0]: stream, [L]: warp-chunk
+  const void *stream_single;
+  const void *stream_batch;
+  const void *range_single;  // hybrid kernel: chunks then units from a cursor
+  const void *range_single_unaligned;
+  const void *range_batch;   // [aligned-only, general] pair, see ctl.unaligned
+  const void *range_batch_unaligned;
   int exec_bytes, k, n_seed, off_T, off_F, off_R, ew;
 };
 

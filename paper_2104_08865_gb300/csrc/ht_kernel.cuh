@@ -1,16 +1,16 @@
 // ht_kernel.cuh -- the HalftimeHash hot path for sm_103a (arXiv 2104.08865).
 //
 // One warp hashes one "chunk": 8^L consecutive EHC executions of one string
-// (L = 2 or 3).  Inside the chunk:
-//   thread (x, p), x = lane>>2 in 0..7, p = lane&3 in 0..3, owns block lanes
-//   2p and 2p+1 (one 16-byte load covers both) of executions 8x..8x+7 of
-//   every 64-execution sub-chunk;
+// (L = 1, 2 or 3).  Inside the chunk thread (x, p), x = lane>>2 in 0..7,
+// p = lane&3 in 0..3, owns block lanes 2p and 2p+1 (one 16-byte load covers
+// both) of execution x (L = 1) or of executions 8x..8x+7 of every
+// 64-execution sub-chunk (L = 2, 3);
 //   * EHC (Section 3.3, Section 5.1): 128-bit streaming loads, XOR-only
 //     GF(8) encode, NH with mul.wide.u32 multiply-adds against keys held in
 //     the constant bank, combine with the paper's small matrices;
-//   * tree level 1 (Section 3.2 node variant, f = 8) in registers, level 2
-//     by warp shuffles across the eight x-threads, level 3 (L = 3) in
-//     registers again;
+//   * tree levels (Section 3.2 node variant, f = 8): with L = 1 level 1 by
+//     warp shuffles across the eight x-threads; with L >= 2 level 1 in
+//     registers, level 2 by shuffles, level 3 (L = 3) in registers again;
 // Above the chunk, levels are finished across warps without waiting: every
 // child adds its NH term of the parent (a sum, so order does not matter) into
 // the parent's accumulator with 64-bit atomics and bumps the parent's arrival
@@ -238,7 +238,28 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
     for (int l = 0; l < 2; ++l)
 #pragma unroll
       for (int t = 0; t < k; ++t) root[l][t] = 0;
-    constexpr int NSUB = (L == 3) ? 8 : 1;
+    if constexpr (L == 1) {
+      // eight executions, one per x-thread; level 1 across the x-threads
+      const int m = (int)((N - e0) < 8 ? (N - e0) : 8);
+      uint64_t y[2][k];
+      if (x < m) ehc2<W, ALIGNED>(sp.ptr + (e0 + (uint64_t)x) * B, p, sh, P, y);
+      if (full) {
+#pragma unroll
+        for (int t = 0; t < k; ++t) {
+          const uint64_t key = x < 7 ? tree_key<W>(P, t, 0, x) : 0;
+#pragma unroll
+          for (int l = 0; l < 2; ++l) root[l][t] = x_sum(x < 7 ? nh64(y[l][t], key) : y[l][t]);
+        }
+      } else if (x < m) {
+        // the last, incomplete group of leaves: pending at level 0, slot x
+#pragma unroll
+        for (int t = 0; t < k; ++t)
+          pend[t] += nh64(y[0][t], final_key<W>(P, t, 0, x, 2 * p)) +
+                     nh64(y[1][t], final_key<W>(P, t, 0, x, 2 * p + 1));
+        anyp = true;
+      }
+    }
+    constexpr int NSUB = (L == 3) ? 8 : (L == 2 ? 1 : 0);
 #pragma unroll 1
     for (int sub = 0; sub < NSUB; ++sub) {
       const uint64_t sb = e0 + 64ull * sub;
@@ -458,69 +479,97 @@ __global__ void __launch_bounds__(256) hash_kernel(const __grid_constant__ KPara
 
 // ---- the batch planner (one block) ---------------------------------------------
 
+// Block-wide exclusive scan of one value per thread (1024 threads at most);
+// returns the exclusive prefix and writes the total to *total.
+__device__ __forceinline__ unsigned long long block_scan(unsigned long long v, unsigned long long *sh,
+                                                         unsigned long long *total) {
+  const unsigned tid = threadIdx.x, nt = blockDim.x;
+  const int ln = tid & 31, wid = tid >> 5;
+  unsigned long long xi = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(kFull, xi, o);
+    if (ln >= o) xi += y;
+  }
+  __syncthreads();
+  if (ln == 31) sh[wid] = xi;
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned nw = nt >> 5;
+    unsigned long long w = ln < (int)nw ? sh[ln] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(kFull, w, o);
+      if (ln >= o) w += y;
+    }
+    if (ln < (int)nw) sh[ln] = w;
+  }
+  __syncthreads();
+  const unsigned long long excl = (xi - v) + (wid ? sh[wid - 1] : 0);
+  *total = sh[(nt >> 5) - 1];
+  __syncthreads();
+  return excl;
+}
+
+// The batch planner (one block of 1024 threads): per string, executions N,
+// work units (L = 0: stream/range units, one per 8 executions plus the tail
+// unit; L >= 1: warp-chunk items of 8^L executions), tree-group slots, full
+// 64-execution chunks, and their prefix sums; then the hybrid kernel's work
+// list: phase A holds every full chunk of the batch but the last
+// total_warps, phase B every remaining unit.
 template <int W, int L>
 __global__ void __launch_bounds__(1024) plan_kernel(const PlanArgs A) {
   constexpr uint64_t B = Dims<W>::exec_bytes;
-  __shared__ unsigned long long s_items[32], s_groups[32];
+  __shared__ unsigned long long sh[32];
   const unsigned tid = threadIdx.x, nt = blockDim.x;
   const unsigned per = (A.count + nt - 1) / nt;
   const unsigned lo = tid * per < A.count ? tid * per : A.count;
   const unsigned hi = lo + per < A.count ? lo + per : A.count;
-  auto groups_of = [](uint64_t N) {
+  auto groups_of = [](uint64_t N) -> unsigned long long {
     uint64_t g = 0;
-    for (int lvl = L; lvl < kLevels; ++lvl) g += N >> (3 * lvl + 3);
+    for (int lvl = (L == 0 ? 1 : L); lvl < kLevels; ++lvl) g += N >> (3 * lvl + 3);
     return g;
   };
-  auto items_of = [](uint64_t N) {
+  auto items_of = [](uint64_t N) -> unsigned long long {
+    if (L == 0) return ((N + 7) >> 3) + 1;
     const uint64_t it = (N + (1ull << (3 * L)) - 1) >> (3 * L);
     return it ? it : 1ull;
   };
-  unsigned long long my_items = 0, my_groups = 0;
+  unsigned long long my_items = 0, my_groups = 0, my_chunks = 0;
+  bool my_unaligned = false;
   for (unsigned i = lo; i < hi; ++i) {
     const uint64_t N = A.lens[i] / B;
     my_items += items_of(N);
     my_groups += groups_of(N);
+    my_chunks += N >> 6;
+    my_unaligned |= (((uintptr_t)A.ptrs[i]) & 15u) != 0;
   }
-  // block-wide exclusive scan of (items, groups)
-  const int ln = tid & 31, wid = tid >> 5;
-  unsigned long long xi = my_items, xg = my_groups;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long yi = __shfl_up_sync(kFull, xi, o);
-    const unsigned long long yg = __shfl_up_sync(kFull, xg, o);
-    if (ln >= o) {
-      xi += yi;
-      xg += yg;
+  const int any_unaligned = __syncthreads_or(my_unaligned);
+  unsigned long long total_i, total_g, total_c;
+  unsigned long long base_i = block_scan(my_items, sh, &total_i);
+  unsigned long long base_g = block_scan(my_groups, sh, &total_g);
+  unsigned long long base_c = block_scan(my_chunks, sh, &total_c);
+  // phase A: every full chunk but the last nw (one per warp), whole
+  const unsigned long long nw = A.total_warps ? A.total_warps : 1;
+  const unsigned long long cut = total_c > nw ? total_c - nw : 0;
+  unsigned long long my_b = 0;
+  {
+    unsigned long long c0 = base_c;
+    for (unsigned i = lo; i < hi; ++i) {
+      const uint64_t N = A.lens[i] / B;
+      const unsigned long long C2 = N >> 6;
+      const unsigned long long a = cut > c0 ? (cut - c0 < C2 ? cut - c0 : C2) : 0;
+      my_b += items_of(N) - 8 * a;
+      c0 += C2;
     }
   }
-  if (ln == 31) {
-    s_items[wid] = xi;
-    s_groups[wid] = xg;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    const unsigned nw = nt >> 5;
-    unsigned long long vi = ln < (int)nw ? s_items[ln] : 0, vg = ln < (int)nw ? s_groups[ln] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long yi = __shfl_up_sync(kFull, vi, o);
-      const unsigned long long yg = __shfl_up_sync(kFull, vg, o);
-      if (ln >= o) {
-        vi += yi;
-        vg += yg;
-      }
-    }
-    if (ln < (int)nw) {
-      s_items[ln] = vi;
-      s_groups[ln] = vg;
-    }
-  }
-  __syncthreads();
-  unsigned long long base_i = (xi - my_items) + (wid ? s_items[wid - 1] : 0);
-  unsigned long long base_g = (xg - my_groups) + (wid ? s_groups[wid - 1] : 0);
+  unsigned long long total_b;
+  unsigned long long base_b = block_scan(my_b, sh, &total_b);
   for (unsigned i = lo; i < hi; ++i) {
     const uint64_t len = A.lens[i];
     const uint64_t N = len / B;
+    const unsigned long long C2 = N >> 6;
+    const unsigned long long a = cut > base_c ? (cut - base_c < C2 ? cut - base_c : C2) : 0;
     StrPlan sp;
     sp.ptr = static_cast<const uint8_t *>(A.ptrs[i]);
     sp.len = len;
@@ -529,42 +578,29 @@ __global__ void __launch_bounds__(1024) plan_kernel(const PlanArgs A) {
     sp.grp0 = base_g;
     sp.n_items = (uint32_t)items_of(N);
     sp.pad = 0;
+    sp.chunk0 = base_c;
+    sp.chunks_a = a;
+    sp.unitb0 = base_b;
     A.plans[i] = sp;
     A.item0s[i] = base_i;
+    A.chunk0s[i] = base_c;
+    A.unitb0s[i] = base_b;
     base_i += items_of(N);
     base_g += groups_of(N);
+    base_c += C2;
+    base_b += items_of(N) - 8 * a;
   }
   if (tid == nt - 1) {
-    const unsigned long long total_i = s_items[(nt >> 5) - 1];
-    const unsigned long long total_g = s_groups[(nt >> 5) - 1];
     A.item0s[A.count] = total_i;
+    A.chunk0s[A.count] = total_c;
+    A.unitb0s[A.count] = total_b;
     A.ctl->total = total_i;
     A.ctl->groups = total_g;
+    A.ctl->chunks_a = cut;
+    A.ctl->units_b = total_b;
+    A.ctl->unaligned = any_unaligned ? 1u : 0u;
     if (total_g > A.cap_groups) A.ctl->status = kStatusTooLong;
   }
-}
-
-// ---- kernel tables --------------------------------------------------------------
-
-template <int W>
-KernelSet make_kernel_set() {
-  KernelSet ks;
-  ks.single_aligned[0] = (const void *)hash_kernel<W, 2, true, true>;
-  ks.single_aligned[1] = (const void *)hash_kernel<W, 3, true, true>;
-  ks.single_unaligned[0] = (const void *)hash_kernel<W, 2, true, false>;
-  ks.single_unaligned[1] = (const void *)hash_kernel<W, 3, true, false>;
-  ks.batch[0] = (const void *)hash_kernel<W, 2, false, false>;
-  ks.batch[1] = (const void *)hash_kernel<W, 3, false, false>;
-  ks.plan[0] = (const void *)plan_kernel<W, 2>;
-  ks.plan[1] = (const void *)plan_kernel<W, 3>;
-  ks.exec_bytes = Dims<W>::exec_bytes;
-  ks.k = Spec<W>::k;
-  ks.n_seed = Dims<W>::n_seed;
-  ks.off_T = Dims<W>::off_T;
-  ks.off_F = Dims<W>::off_F;
-  ks.off_R = Dims<W>::off_R;
-  ks.ew = Dims<W>::ew;
-  return ks;
 }
 
 }  // namespace ht

@@ -1,6 +1,6 @@
 // Kernel instantiations for HalftimeHash40 (one translation unit per width
 // so the four widths compile in parallel).
-#include "ht_kernel.cuh"
+#include "ht_range.cuh"
 
 namespace ht {
 const KernelSet &kernels_w40() {

@@ -16,6 +16,7 @@ struct ht_ctx {
   int width = 0;
   int device = 0;
   int num_sms = 1;
+  int smem_optin = 0;  // max dynamic shared memory per block
   const ht::KernelSet *ks = nullptr;
   std::vector<uint64_t> h_seeds;
   unsigned long long *d_seeds = nullptr;
@@ -27,6 +28,8 @@ struct ht_ctx {
   unsigned int *str_done = nullptr;
   ht::StrPlan *plans = nullptr;
   unsigned long long *item0s = nullptr;
+  unsigned long long *chunk0s = nullptr;
+  unsigned long long *unitb0s = nullptr;
   ht::Ctl *ctl = nullptr;
   uint64_t cap_groups = 0, cap_strings = 0;
   // launch shapes: [0..63] by floor(log2(len)), [64] batches
@@ -34,8 +37,7 @@ struct ht_ctx {
   // batch graph: planner -> persistent kernel
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
-  cudaGraphNode_t node_plan = nullptr, node_hash = nullptr;
-  cudaKernelNodeParams node_hash_params = {};
+  cudaGraphNode_t node_plan = nullptr, node_hash = nullptr, node_hash2 = nullptr;
   ht_shape graph_shape = {};
   bool graph_valid = false;
   ht::PlanArgs plan_args = {};

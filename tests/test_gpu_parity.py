@@ -96,16 +96,32 @@ def _boundary_lengths(width):
     return out
 
 
-@pytest.mark.parametrize("width", WIDTHS)
-@pytest.mark.parametrize("L", [2, 3])
-def test_chunk_and_tree_boundaries(dev, width, L):
-    """Execution counts around every f^l boundary (partial chunks, pending
-    roots at each level, complete upper groups) with ragged tails, for both
-    chunk heights."""
+SHAPES = {
+    "stream-r2-w8": dict(kernel=0, stages=2, threads_per_block=256, blocks_per_sm=1),
+    "stream-r3-w6": dict(kernel=0, stages=3, threads_per_block=192, blocks_per_sm=1),
+    "stream-r4-w2x2": dict(kernel=0, stages=4, threads_per_block=64, blocks_per_sm=2),
+    "range-256x2": dict(kernel=2, threads_per_block=256, blocks_per_sm=2),
+    "range-64x1": dict(kernel=2, threads_per_block=64, blocks_per_sm=1),
+    "chunk-L1": dict(kernel=1, chunk_levels=1, threads_per_block=256, blocks_per_sm=32),
+    "chunk-L2": dict(kernel=1, chunk_levels=2, threads_per_block=256, blocks_per_sm=32),
+    "chunk-L3": dict(kernel=1, chunk_levels=3, threads_per_block=128, blocks_per_sm=32),
+}
+
+
+def _set_all(h, shape):
     from paper_2104_08865_gb300 import abi
+    for n in [1 << b for b in range(64)] + [2**64 - 1]:
+        abi.ht_set_shape(h.ctx, n, **shape)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+@pytest.mark.parametrize("shape", sorted(SHAPES))
+def test_chunk_and_tree_boundaries(dev, width, shape):
+    """Execution counts around every f^l boundary (partial stages and chunks,
+    pending roots at each level, complete upper groups) with ragged tails,
+    for both kernel families and several launch shapes."""
     h, ref = _pair(width, seed=11)
-    for n in (0, 1 << 10, 1 << 16, 1 << 20, 1 << 24, 1 << 30, 2**64 - 1):
-        abi.ht_set_shape(h.ctx, n, L, 256, 32)
+    _set_all(h, SHAPES[shape])
     lens = _boundary_lengths(width)
     buf, offs = inputs.packed_batch(21, lens)
     want = oracle.hash_many(width, ref, buf, offs, lens)
@@ -115,9 +131,11 @@ def test_chunk_and_tree_boundaries(dev, width, L):
 
 
 @pytest.mark.parametrize("width", WIDTHS)
-def test_unaligned_strings(dev, width):
+@pytest.mark.parametrize("shape", ["stream-r3-w6", "chunk-L2", "range-256x2"])
+def test_unaligned_strings(dev, width, shape):
     """Strings starting at every byte offset 1..15 past a 16-byte boundary."""
     h, ref = _pair(width, seed=3)
+    _set_all(h, SHAPES[shape])
     xb = oracle.params(width)["exec_bytes"]
     lens = [5, xb - 1, xb + 3, 64 * xb + 11, 70 * xb + 100]
     src = inputs.stream_bytes(9, 0, max(lens) + 64)
@@ -141,17 +159,22 @@ def test_c2_one_gib_string(dev, width):
     host = dbuf.cpu().numpy()
     want = oracle.hash_bytes(width, ref, host)
     assert np.array_equal(got, want)
+    for name in ("chunk-L2", "stream-r3-w6"):
+        _set_all(h, SHAPES[name])
+        assert np.array_equal(_u64(h.hash(dbuf)), want), name
     pinned = torch.empty(n, dtype=torch.uint8).pin_memory()
     pinned.copy_(torch.from_numpy(host))
     assert np.array_equal(h.hash_host(pinned.numpy()), want)
 
 
-def test_c4_batch_50000_log_uniform(dev):
+@pytest.mark.parametrize("shape", ["stream-r3-w6", "chunk-L2", "range-256x2"])
+def test_c4_batch_50000_log_uniform(dev, shape):
     """50,000 strings, lengths log-uniform in [64 B, 1 MiB] (splitmix64 seed 3),
-    HH24: the persistent batch launch, one launch per string and the oracle
-    agree on every digest."""
+    HH24: the batch launch, one launch per string and the oracle agree on
+    every digest."""
     width = 24
     h, ref = _pair(width)
+    _set_all(h, SHAPES[shape])
     lens = inputs.log_uniform_lengths(3, 50_000, 64, 1 << 20)
     buf, offs = inputs.packed_batch(3, lens)
     dbuf = torch.from_numpy(buf).to(dev)
@@ -169,7 +192,7 @@ def test_autotuned_shape_keeps_digests(dev, width):
     h, ref = _pair(width)
     n = 48 << 20
     best = abi.ht_autotune(h.ctx, n)
-    assert best["chunk_levels"] in (2, 3)
+    assert best["kernel"] in (0, 1)
     assert abi.ht_get_shape(h.ctx, n) == best
     dbuf = inputs.stream_bytes_torch(5, 0, n + 333, dev)
     want = oracle.hash_bytes(width, ref, dbuf.cpu().numpy())
@@ -185,7 +208,8 @@ def test_launch_counter_counts_kernels(dev):
     ln = torch.tensor([10, 1000, 100000], dtype=torch.int64, device=dev)
     h.hash_batch(ptrs, ln, 3)
     torch.cuda.synchronize()
-    assert h.launches() - before == 3  # one hash kernel + planner + batch kernel
+    # one hash kernel, then planner + the batch kernel pair of the range family
+    assert h.launches() - before == 4
 
 
 @pytest.mark.parametrize("width", WIDTHS)
