@@ -146,6 +146,36 @@ int ht_hash_batch_naive(ht_ctx *ctx, const void *const *ptrs_host,
                         const uint64_t *lens_host, size_t count,
                         uint64_t *digests_dev, ht_stream_t stream);
 
+/* ---- hashing without allocation ---------------------------------------------
+ * (The paper has no counterpart: this serves deployments, not the method.)
+ * Some callers cannot allocate device memory: code running inside another
+ * framework's allocator hooks (allocating there would re-enter the
+ * allocator), processes whose device memory is held by another framework's
+ * memory pool (an extra cudaMalloc fails or breaks that pool's accounting),
+ * and latency-critical paths that cannot take the device synchronisation of
+ * cudaMalloc/cudaFree.  They cannot create an ht_ctx.  ht_hash_noalloc hashes
+ * one device-resident string with the warp-chunk kernel, using scratch that
+ * the library reserves when it is loaded: one 8 MiB __device__ array,
+ * present on every GPU that loads the library until the process exits.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - seed_words_host: the n_words = ht_seed_words(width_bytes) seed words on
+ *     the host; they are copied into the array on `stream`.
+ *   - data_dev / len / digest_dev / stream: as ht_hash (k digest words).
+ *   - Limit: the tree scratch of the array holds 63107 / 42501 / 32039 /
+ *     25710 node groups for widths 16 / 24 / 32 / 40, enough for strings of
+ *     about 32 / 25 / 19 / 11 GB; longer strings return HT_ERR_TOO_LONG with
+ *     no GPU work.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array and clears the parts it uses at the
+ *     start, so calls that overlap on the GPU (other streams, other host
+ *     threads) race and give wrong digests: order them.
+ * Errors: HT_ERR_WIDTH, HT_ERR_ARG, HT_ERR_TOO_LONG, HT_ERR_CUDA. */
+int ht_hash_noalloc(int width_bytes, const uint64_t *seed_words_host,
+                    size_t n_words, const void *data_dev, uint64_t len,
+                    uint64_t *digest_dev, ht_stream_t stream);
+
 /* ---- launch shapes and autotuning ------------------------------------------
  * Three kernel families compute the same digests:
  *   kernel 0, the stream kernel: every warp owns a ring of `stages`

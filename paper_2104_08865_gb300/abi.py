@@ -81,6 +81,7 @@ _PROTOS = {
     "ht_hash_host": (_int, [_vp, _vp, _u64, _vp, _vp]),
     "ht_hash_batch": (_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "ht_hash_batch_naive": (_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
+    "ht_hash_noalloc": (_int, [_int, _u64p, _sz, _vp, _u64, _vp, _vp]),
     "ht_autotune": (_int, [_vp, _u64, _vp, ctypes.POINTER(ht_shape)]),
     "ht_get_shape": (_int, [_vp, _u64, ctypes.POINTER(ht_shape)]),
     "ht_set_shape": (_int, [_vp, _u64, ctypes.POINTER(ht_shape)]),
@@ -210,6 +211,13 @@ def ht_hash_batch_naive(ctx: int, ptrs_host, lens_host, count: int, digests_dev,
                         stream=None) -> None:
     _check(_lib.ht_hash_batch_naive(ctx, _ptr(ptrs_host), _ptr(lens_host), count,
                                     _ptr(digests_dev), _stream(stream)))
+
+
+def ht_hash_noalloc(width: int, seed_words, data_dev, length: int, digest_dev, stream=None) -> None:
+    """Hash without any allocation (scratch in the library's fixed device array)."""
+    seed_words = np.ascontiguousarray(seed_words, dtype=np.uint64)
+    _check(_lib.ht_hash_noalloc(width, seed_words.ctypes.data_as(_u64p), seed_words.size,
+                                _ptr(data_dev), length, _ptr(digest_dev), _stream(stream)))
 
 
 def ht_autotune(ctx: int, length: int, stream=None) -> dict:
