@@ -248,6 +248,16 @@ int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t 
   const uint64_t per_warp = shape.kernel != 1 ? 4 : 1;
   const uint64_t want = (u_end - u_begin + per_warp * wpb - 1) / (per_warp * wpb);
   uint64_t grid = std::min<uint64_t>((uint64_t)c->num_sms * bps, want);
+  if (shape.kernel == 1) {
+    // whole rounds: with R = ceil(items / max warps) rounds of cursor
+    // grabs, ceil(items / R) warps finish together instead of a last round
+    // that only a few warps work on
+    const uint64_t items = u_end - u_begin;
+    const uint64_t wmax = (uint64_t)c->num_sms * bps * wpb;
+    const uint64_t rounds = (items + wmax - 1) / wmax;
+    const uint64_t warps = (items + rounds - 1) / rounds;
+    grid = std::min(grid, (warps + wpb - 1) / wpb);
+  }
   grid = std::max<uint64_t>(grid, 1);
   KParams P;
   fill_keys(c, P);

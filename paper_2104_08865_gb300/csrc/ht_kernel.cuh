@@ -274,8 +274,9 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
         for (int t = 0; t < k; ++t) n1[l][t] = 0;
       const uint8_t *ex = sp.ptr + (sb + 8ull * x) * B;
       if (cnt == 8) {
-        // eight leaves -> one level-1 node per (tree, lane), in registers
-#pragma unroll 1
+        // eight leaves -> one level-1 node per (tree, lane), in registers;
+        // two executions per iteration keep two loads batches in flight
+#pragma unroll 2
         for (int s = 0; s < 8; ++s) {
           uint64_t y[2][k];
           ehc2<W, ALIGNED>(ex + s * B, p, sh, P, y);
