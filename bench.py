@@ -164,6 +164,124 @@ def run_reference(args):
     return 0
 
 
+def _aligned_offsets(lens, align=256):
+    import numpy as np
+    slots = (np.asarray(lens, dtype=np.int64) + align - 1) // align * align
+    offs = np.concatenate([[0], np.cumsum(slots)[:-1]]).astype(np.int64)
+    return offs, int(slots.sum())
+
+
+def run_batch(args, dev, stream):
+    """C4: 50,000 strings, lengths log-uniform in [64 B, 1 MiB] (splitmix64
+    seed 3), width 24: one graph-replayed batch launch vs one launch per
+    string.  String i occupies bytes [off_i, off_i + len_i) of the seed-3
+    stream, with off_i 256-byte aligned."""
+    import numpy as np
+    import torch
+
+    from paper_2104_08865_gb300 import Hasher, abi, inputs
+    count = args.batch_strings
+    lens = inputs.log_uniform_lengths(3, count, 64, 1 << 20)
+    offs, total = _aligned_offsets(lens)
+    buf = inputs.stream_bytes_torch(3, 0, total + 256, dev)
+    ptrs = torch.tensor(buf.data_ptr() + offs, dtype=torch.int64, device=dev)
+    lt = torch.tensor(lens, dtype=torch.int64, device=dev)
+    h = Hasher(24, seed_words=abi.ht_seed_expand(SEED_KEY, 24))
+    out = torch.empty((count, 3), dtype=torch.int64, device=dev)
+    for _ in range(3):
+        abi.ht_hash_batch(h.ctx, ptrs, lt, count, out, stream)
+    torch.cuda.synchronize()
+    h.status()
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = h.launches()
+    e0.record(stream)
+    for _ in range(reps):
+        abi.ht_hash_batch(h.ctx, ptrs, lt, count, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / reps
+    launches_batch = (h.launches() - l0) // reps
+    nbytes = int(lens.sum())
+    naive = torch.empty_like(out)
+    hp = (buf.data_ptr() + offs).astype(np.uint64)
+    h.hash_batch_naive(hp, lens, naive)  # warm-up
+    torch.cuda.synchronize()
+    e0.record(stream)
+    h.hash_batch_naive(hp, lens, naive)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_naive = e0.elapsed_time(e1)
+    same = bool(torch.equal(out, naive))
+    h.close()
+    return {"workload": "%d strings, log-uniform 64 B..1 MiB, %.2f GB, width 24" % (count, nbytes / 1e9),
+            "batch_gbs": round(nbytes / ms_batch / 1e6, 1), "batch_ms": round(ms_batch, 3),
+            "batch_launches": launches_batch,
+            "naive_gbs": round(nbytes / ms_naive / 1e6, 1), "naive_ms": round(ms_naive, 3),
+            "naive_launches": count, "speedup": round(ms_naive / ms_batch, 2),
+            "digests_equal": same}
+
+
+def run_serving(args, dev, stream):
+    """C5: Poisson arrivals of width-32 hash requests, lengths log-uniform in
+    [256 B, 64 MiB], 16 GiB admission budget; offered load swept over
+    fractions of the peak measured for each form (device-resident requests,
+    and pinned host requests copied in by the server)."""
+    import numpy as np
+    import torch
+
+    from paper_2104_08865_gb300 import Hasher, abi, inputs
+    rng = np.random.default_rng(6)
+    pool_bytes = args.serve_pool
+    pool_dev = inputs.stream_bytes_torch(5, 0, pool_bytes, dev)
+    pool_host = torch.empty(pool_bytes, dtype=torch.uint8).pin_memory()
+    pool_host.copy_(pool_dev)
+    torch.cuda.synchronize()
+    h = Hasher(32, seed_words=abi.ht_seed_expand(SEED_KEY, 32))
+    mean_len = None
+    out = {"workload": "width 32, lengths log-uniform 256 B..64 MiB, Poisson arrivals, budget 16 GiB, "
+                       "%.1f s per load point" % args.serve_seconds, "forms": {}}
+
+    def requests(n, seed):
+        ln = inputs.log_uniform_lengths(seed, n, 256, 64 << 20)
+        off = (rng.integers(0, pool_bytes - (64 << 20), n) // 256) * 256
+        return ln, off
+
+    for form, base, pinned in (("device", pool_dev.data_ptr(), 0),
+                               ("pinned_h2d", pool_host.data_ptr(), 1)):
+        res = {}
+        # peak: a burst with every request arriving at once
+        nburst = 1500 if form == "device" else 300
+        ln, off = requests(nburst, 61)
+        srv = abi.ht_server_create(h.ctx, 16 << 30, n_streams=4, max_batch=4096)
+        dig = np.zeros((nburst, 4), dtype=np.uint64)
+        abi.ht_server_replay(srv, base + off, ln, [pinned] * nburst, np.zeros(nburst), dig)
+        st = abi.ht_server_stats(srv, reset=True)
+        peak = st["bytes_completed"] / st["wall_s"] / 1e9
+        res["peak_gbs"] = round(peak, 1)
+        mean_len = float(inputs.log_uniform_lengths(62, 100000, 256, 64 << 20).mean())
+        res["points"] = []
+        for frac in args.serve_loads:
+            rate = frac * peak * 1e9 / mean_len  # requests per second
+            n = max(50, int(rate * args.serve_seconds))
+            ln, off = requests(n, 63)
+            gaps = rng.exponential(1e6 / rate, n)
+            arr = np.cumsum(gaps) - gaps[0]
+            dig = np.zeros((n, 4), dtype=np.uint64)
+            late = abi.ht_server_replay(srv, base + off, ln, [pinned] * n, arr, dig)
+            st = abi.ht_server_stats(srv, reset=True)
+            res["points"].append({"load": frac, "offered_gbs": round(frac * peak, 1),
+                                  "requests": n, "achieved_gbs": round(st["bytes_completed"] / st["wall_s"] / 1e9, 1),
+                                  "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
+                                  "max_submit_delay_us": round(late, 1)})
+        abi.ht_server_destroy(srv)
+        out["forms"][form] = res
+    out["mean_len_bytes"] = round(mean_len)
+    h.close()
+    del pool_host
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -289,6 +407,9 @@ def run_gpu(args):
                          "per width (%.1f s)" % (sample >> 20, dt),
                "digests_match_gpu": match}
 
+    batch = run_batch(args, dev, stream) if (rank == 0 and not args.no_batch) else None
+    serving = run_serving(args, dev, stream) if (rank == 0 and not args.no_serve) else None
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": ws,
@@ -308,6 +429,7 @@ def run_gpu(args):
                          "peak_source": peak_kind},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": ck,
             "shapes": shapes,
+            "batch": batch, "serving": serving,
             "digests": {str(w): ["%016x" % v for v in digests[w]] for w in WIDTHS},
         }
         print(json.dumps(line), flush=True)
@@ -330,6 +452,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-bytes", type=int, default=GIB)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-strings", type=int, default=50_000)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-pool", type=int, default=2 * GIB)
+    ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",")],
+                    default=[0.1, 0.5, 0.9, 1.2])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.steps > 2:
         args.warmup = 3

@@ -267,6 +267,20 @@ int ht_server_wait(ht_server *srv, uint64_t ticket, uint64_t timeout_us);
  * already launched or finished, or HT_ERR_ARG (unknown ticket). */
 int ht_server_cancel(ht_server *srv, uint64_t ticket);
 
+/* Load replay: submits request i (ptrs[i], lens[i], pinned[i] as in
+ * ht_server_submit; pinned may be NULL for all-device requests) at
+ * arrival_us[i] microseconds after the call starts (non-decreasing offsets;
+ * the submitting thread spins on the clock between arrivals), writing its
+ * digest to digests_host + i*k, then waits for all of them (bounded by
+ * timeout_us after the last arrival).  A request the queue refuses (HT_ERR_BUSY)
+ * is retried until it is admitted.  *late_us (if not NULL) receives the
+ * largest delay between a request's scheduled arrival and its submission.
+ * Errors: HT_ERR_ARG, HT_ERR_BUDGET, HT_ERR_TIMEOUT, or the first failed
+ * request's error. */
+int ht_server_replay(ht_server *srv, const void *const *ptrs, const uint64_t *lens,
+                     const int *pinned, const double *arrival_us, size_t n,
+                     uint64_t *digests_host, uint64_t timeout_us, double *late_us);
+
 /* Blocks until every submitted request has completed or timeout_us passes. */
 int ht_server_drain(ht_server *srv, uint64_t timeout_us);
 

@@ -94,6 +94,7 @@ _PROTOS = {
     "ht_server_wait": (_int, [_vp, _u64, _u64]),
     "ht_server_cancel": (_int, [_vp, _u64]),
     "ht_server_drain": (_int, [_vp, _u64]),
+    "ht_server_replay": (_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp, _u64, ctypes.POINTER(ctypes.c_double)]),
     "ht_server_stats": (_int, [_vp, ctypes.POINTER(ht_server_stats_t), _int]),
     "ht_server_latencies": (_sz, [_vp, ctypes.POINTER(ctypes.c_double), _sz]),
     "ht_server_destroy": (_int, [_vp]),
@@ -281,6 +282,21 @@ def ht_server_wait(srv: int, ticket: int, timeout_us: int) -> None:
 
 def ht_server_cancel(srv: int, ticket: int) -> None:
     _check(_lib.ht_server_cancel(srv, ticket))
+
+
+def ht_server_replay(srv: int, ptrs, lens, pinned, arrival_us, digests_host,
+                     timeout_us: int = 60_000_000) -> float:
+    """Replays requests at the given arrival offsets; returns the worst
+    submission delay (us)."""
+    ptrs = np.ascontiguousarray(ptrs, dtype=np.uint64)
+    lens = np.ascontiguousarray(lens, dtype=np.uint64)
+    arr = np.ascontiguousarray(arrival_us, dtype=np.float64)
+    pin = None if pinned is None else np.ascontiguousarray(pinned, dtype=np.int32)
+    late = ctypes.c_double()
+    _check(_lib.ht_server_replay(srv, ptrs.ctypes.data, lens.ctypes.data,
+                                 None if pin is None else pin.ctypes.data, arr.ctypes.data,
+                                 len(lens), _ptr(digests_host), timeout_us, ctypes.byref(late)))
+    return late.value
 
 
 def ht_server_drain(srv: int, timeout_us: int) -> None:

@@ -487,6 +487,36 @@ int ht_server_drain(ht_server *S, uint64_t timeout_us) {
                                     (unsigned long long)timeout_us);
 }
 
+int ht_server_replay(ht_server *S, const void *const *ptrs, const uint64_t *lens, const int *pinned,
+                     const double *arrival_us, size_t n, uint64_t *digests_host, uint64_t timeout_us,
+                     double *late_us) {
+  if (!S || (n && (!ptrs || !lens || !arrival_us || !digests_host)))
+    return ht::set_error(HT_ERR_ARG, "ht_server_replay: bad arguments");
+  std::vector<uint64_t> tickets(n);
+  const int64_t t0 = now_ns();
+  double worst = 0.0;
+  for (size_t i = 0; i < n; ++i) {
+    const int64_t due = t0 + (int64_t)(arrival_us[i] * 1000.0);
+    while (now_ns() < due) {
+    }
+    for (;;) {
+      const int rc = ht_server_submit(S, ptrs[i], lens[i], pinned ? pinned[i] : 0,
+                                      digests_host + i * (size_t)S->k, &tickets[i]);
+      if (rc == HT_OK) break;
+      if (rc != HT_ERR_BUSY) return rc;
+      std::this_thread::yield();
+    }
+    worst = std::max(worst, (now_ns() - due) / 1000.0);
+  }
+  if (late_us) *late_us = worst;
+  int first_err = HT_OK;
+  for (size_t i = 0; i < n; ++i) {
+    const int rc = ht_server_wait(S, tickets[i], timeout_us);
+    if (rc != HT_OK && first_err == HT_OK) first_err = rc;
+  }
+  return first_err;
+}
+
 int ht_server_cancel(ht_server *S, uint64_t ticket) {
   if (!S) return ht::set_error(HT_ERR_ARG, "ht_server_cancel: NULL server");
   std::lock_guard<std::mutex> g(S->mu);

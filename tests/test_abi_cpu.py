@@ -171,3 +171,21 @@ def test_fake_server_concurrent_submitters(built):
         assert st["bytes_completed"] == sum(64 + i for i in range(400))
     finally:
         abi.ht_server_destroy(srv)
+
+
+def test_fake_server_replay_follows_arrival_times(built):
+    from paper_2104_08865_gb300 import abi
+    srv = abi.ht_server_create_fake(24, 1 << 30, batch_delay_us=200, n_streams=4, max_batch=64)
+    try:
+        n = 300
+        arrivals = np.linspace(0, 30_000, n)  # 30 ms
+        digs = np.ones((n, 3), dtype=np.uint64)
+        t0 = time.time()
+        late = abi.ht_server_replay(srv, [0x1000] * n, [4096] * n, None, arrivals, digs)
+        assert time.time() - t0 >= 0.03
+        assert late < 20_000
+        assert not digs.any()
+        st = abi.ht_server_stats(srv)
+        assert st["completed"] == n and st["p99_us"] >= 200
+    finally:
+        abi.ht_server_destroy(srv)

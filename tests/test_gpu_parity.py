@@ -224,3 +224,88 @@ def test_rekey_matches_fresh_context(dev, width):
     data = inputs.stream_bytes(6, 0, 3 * 64 * oracle.params(width)["exec_bytes"] + 5)
     got = _u64(h.hash(torch.from_numpy(data).to(dev)))
     assert np.array_equal(got, oracle.hash_bytes(width, ref2, data))
+
+
+def test_serving_alone_vs_mix(dev):
+    """Requests of mixed sizes (device-resident and pinned host) arrive while
+    others are on the GPU; every digest equals the one hashed alone, and the
+    oracle's on a sample."""
+    from paper_2104_08865_gb300 import abi
+    width = 32
+    h, ref = _pair(width)
+    rng = np.random.default_rng(12)
+    n = 240
+    pool = 96 << 20
+    pool_dev = inputs.stream_bytes_torch(7, 0, pool, dev)
+    pool_host = torch.empty(pool, dtype=torch.uint8).pin_memory()
+    pool_host.copy_(pool_dev)
+    torch.cuda.synchronize()
+    lens = inputs.log_uniform_lengths(13, n, 256, 4 << 20)
+    offs = rng.integers(0, pool - (4 << 20), n)  # any alignment
+    pinned = rng.integers(0, 2, n).astype(np.int32)
+    ptrs = np.where(pinned == 1, pool_host.data_ptr() + offs, pool_dev.data_ptr() + offs)
+    arrivals = np.sort(rng.uniform(0, 20_000, n))
+    srv = abi.ht_server_create(h.ctx, 256 << 20, n_streams=3, max_batch=32)
+    try:
+        dig = np.zeros((n, 4), dtype=np.uint64)
+        abi.ht_server_replay(srv, ptrs, lens, pinned, arrivals, dig)
+        st = abi.ht_server_stats(srv)
+        assert st["completed"] == n and st["batches"] > 1
+    finally:
+        abi.ht_server_destroy(srv)
+    alone = torch.empty((n, 4), dtype=torch.int64, device=dev)
+    for i in range(n):
+        h.hash(pool_dev, int(lens[i]), out=alone[i], offset=int(offs[i]))
+    assert np.array_equal(dig, _u64(alone))
+    host = pool_dev.cpu().numpy()
+    for i in range(0, n, 12):
+        o, ln = int(offs[i]), int(lens[i])
+        assert np.array_equal(dig[i], oracle.hash_bytes(width, ref, host[o:o + ln]))
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_c3_collision_sweep(dev, width):
+    """100,000 pairs of 64 KiB random strings (splitmix64 seed 4) that differ
+    in one 32-bit word, hashed under 1,000 seeds (splitmix64 seed 11 outputs):
+    no full-width collision (the bound of Section 6.2 predicts ~1e-10), the top
+    16 bits of output 0 collide at about 2^-16, and a 10^4-hash sample agrees
+    with the oracle bit for bit."""
+    import math
+    from paper_2104_08865_gb300 import abi
+    pairs, n, seeds = 100_000, 1 << 16, 1000
+    rng = np.random.default_rng(width)
+    both = torch.empty((2, pairs, n), dtype=torch.uint8, device=dev)
+    both[0].copy_(inputs.stream_bytes_torch(4, 0, pairs * n, dev).view(pairs, n))
+    both[1].copy_(both[0])
+    base, flipped = both[0], both[1]
+    words = flipped.view(torch.int32)
+    pos = torch.from_numpy(rng.integers(0, n // 4, pairs)).to(dev)
+    flip = torch.from_numpy(rng.integers(1, 2**32, pairs, dtype=np.uint64).astype(np.uint32).view(np.int32)).to(dev)
+    rows = torch.arange(pairs, device=dev)
+    words[rows, pos] ^= flip
+    ptrs = both.data_ptr() + torch.arange(2 * pairs, device=dev, dtype=torch.int64) * n
+    lens = torch.full((2 * pairs,), n, dtype=torch.int64, device=dev)
+    seed64 = inputs.splitmix64_words(11, 0, seeds)
+    h, _ = _pair(width)
+    abi.ht_ctx_reserve(h.ctx, 2 * pairs * n, 2 * pairs)
+    k = width // 8
+    out = torch.empty((2 * pairs, k), dtype=torch.int64, device=dev)
+    full = 0
+    top = 0
+    for i in range(seeds):
+        abi.ht_ctx_rekey(h.ctx, abi.ht_seed_expand(int(seed64[i]), width))
+        abi.ht_hash_batch(h.ctx, ptrs, lens, 2 * pairs, out)
+        a, b = out[:pairs], out[pairs:]
+        full += int(torch.all(a == b, dim=1).sum())
+        top += int(((a[:, 0] >> 48) == (b[:, 0] >> 48)).sum())
+        if i == 0:
+            sample = _u64(torch.cat([a[:5000], b[:5000]]))
+    h.status()
+    assert full == 0
+    expect = seeds * pairs / 65536.0
+    assert abs(top - expect) < 6 * math.sqrt(expect), (top, expect)
+    ref = oracle.seed_expand(int(seed64[0]), oracle.seed_words(width))
+    host = torch.cat([base[:5000], flipped[:5000]]).cpu().numpy().reshape(-1)
+    offs = np.arange(10_000, dtype=np.int64) * n
+    want = oracle.hash_many(width, ref, host, offs, [n] * 10_000)
+    assert np.array_equal(sample, want)
