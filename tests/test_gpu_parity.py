@@ -267,10 +267,11 @@ def test_serving_alone_vs_mix(dev):
 def test_c3_collision_sweep(dev, width):
     """100,000 pairs of 64 KiB random strings (splitmix64 seed 4) that differ
     in one 32-bit word, hashed under 1,000 seeds (splitmix64 seed 11 outputs):
-    no full-width collision (the bound of Section 6.2 predicts ~1e-10), the top
-    16 bits of output 0 collide at about 2^-16, and a 10^4-hash sample agrees
-    with the oracle bit for bit."""
-    import math
+    no full-width collision among the 10^8 pairs (the bound of Section 6.2,
+    2^-32k (2^kp + h^k + 1), predicts about 1e-10 of them), and a 10^4-hash
+    sample agrees with the oracle bit for bit.  (Narrow windows of a digest
+    are not tested for uniformity: a changed NH term moves the output by a
+    product (d + s) * delta, whose high bits are far from uniform.)"""
     from paper_2104_08865_gb300 import abi
     pairs, n, seeds = 100_000, 1 << 16, 1000
     rng = np.random.default_rng(width)
@@ -291,19 +292,15 @@ def test_c3_collision_sweep(dev, width):
     k = width // 8
     out = torch.empty((2 * pairs, k), dtype=torch.int64, device=dev)
     full = 0
-    top = 0
     for i in range(seeds):
         abi.ht_ctx_rekey(h.ctx, abi.ht_seed_expand(int(seed64[i]), width))
         abi.ht_hash_batch(h.ctx, ptrs, lens, 2 * pairs, out)
         a, b = out[:pairs], out[pairs:]
         full += int(torch.all(a == b, dim=1).sum())
-        top += int(((a[:, 0] >> 48) == (b[:, 0] >> 48)).sum())
         if i == 0:
             sample = _u64(torch.cat([a[:5000], b[:5000]]))
     h.status()
     assert full == 0
-    expect = seeds * pairs / 65536.0
-    assert abs(top - expect) < 6 * math.sqrt(expect), (top, expect)
     ref = oracle.seed_expand(int(seed64[0]), oracle.seed_words(width))
     host = torch.cat([base[:5000], flipped[:5000]]).cpu().numpy().reshape(-1)
     offs = np.arange(10_000, dtype=np.int64) * n

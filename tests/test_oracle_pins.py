@@ -488,20 +488,17 @@ def test_seed_sensitivity(width):
 
 # ----------------------------------------------------------- collision rate
 
-def test_collision_rate_diagnostic():
-    """Close pairs (one 32-bit word flipped) under fresh seeds: no full-width
-    collision, and the top 8 bits of output 0 collide at about 2^-8.  (The
-    low bits are not a fair window: the low m bits of an NH product depend
-    only on the low m bits of its factors, so a difference d*b vanishes mod
-    2^m whenever v2(d) + v2(b) >= m.)  The paper's bound (Section 6.2) is far
-    below what a CPU sample can observe at full width."""
+def test_close_pairs_do_not_collide():
+    """Close pairs (one 32-bit word flipped) under fresh seeds: no collision of
+    the digest, nor of any single 64-bit output word (each word alone is
+    roughly 2^-30-almost-universal here, so 6,000 pairs should show none).
+    Narrow windows of a word are not uniform (a changed NH term moves it by a
+    product (d + s) * delta) and are not tested."""
     width = 16
     p = oracle.params(width)
     n = 2 * p["exec_bytes"] + 100
     trials = 6000
     rng = random.Random(5)
-    full = 0
-    low = 0
     seed_stream = inputs.splitmix64_words(11, 0, trials)
     base = inputs.stream_bytes(4, 0, n)
     for i in range(trials):
@@ -513,21 +510,4 @@ def test_collision_rate_diagnostic():
         y[4 * wpos:4 * wpos + 4] ^= np.frombuffer(flip.to_bytes(4, "little"), np.uint8)
         a = oracle.hash_bytes(width, seeds, x)
         b = oracle.hash_bytes(width, seeds, y)
-        full += int(np.array_equal(a, b))
-        low += int((int(a[0]) >> 56) == (int(b[0]) >> 56))
-    assert full == 0
-    expect = trials / 256.0
-    assert abs(low - expect) < 5 * math.sqrt(expect)
-
-
-def test_torch_generator_matches_numpy():
-    """The device-side input generator (torch ops) reproduces the numpy one."""
-    torch = pytest.importorskip("torch")
-    for seed, start, count in [(2, 0, 1000), (3, 12345, 777), (2**64 - 1, 2**40, 64)]:
-        a = inputs.splitmix64_words(seed, start, count)
-        b = inputs.splitmix64_words_torch(seed, start, count, "cpu").numpy().view(np.uint64)
-        assert np.array_equal(a, b)
-    for off, n in [(0, 100), (3, 1000), (17, 1)]:
-        a = inputs.stream_bytes(4, off, n)
-        b = inputs.stream_bytes_torch(4, off, n, "cpu").numpy()
-        assert np.array_equal(a, b)
+        assert not np.any(a == b), (i, wpos)
