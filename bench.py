@@ -250,14 +250,17 @@ def run_serving(args, dev, stream):
     for form, base, pinned in (("device", pool_dev.data_ptr(), 0),
                                ("pinned_h2d", pool_host.data_ptr(), 1)):
         res = {}
-        # peak: a burst with every request arriving at once
-        nburst = 1500 if form == "device" else 300
+        # peak: bursts with every request arriving at once, sized to tens of
+        # milliseconds of work; the better of two
+        nburst = 10000 if form == "device" else 2000
         ln, off = requests(nburst, 61)
         srv = abi.ht_server_create(h.ctx, 16 << 30, n_streams=4, max_batch=4096)
         dig = np.zeros((nburst, 4), dtype=np.uint64)
-        abi.ht_server_replay(srv, base + off, ln, [pinned] * nburst, np.zeros(nburst), dig)
-        st = abi.ht_server_stats(srv, reset=True)
-        peak = st["bytes_completed"] / st["wall_s"] / 1e9
+        peak = 0.0
+        for _ in range(2):
+            abi.ht_server_replay(srv, base + off, ln, [pinned] * nburst, np.zeros(nburst), dig)
+            st = abi.ht_server_stats(srv, reset=True)
+            peak = max(peak, st["bytes_completed"] / st["wall_s"] / 1e9)
         res["peak_gbs"] = round(peak, 1)
         mean_len = float(inputs.log_uniform_lengths(62, 100000, 256, 64 << 20).mean())
         res["points"] = []

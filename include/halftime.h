@@ -270,11 +270,14 @@ int ht_server_cancel(ht_server *srv, uint64_t ticket);
 /* Load replay: submits request i (ptrs[i], lens[i], pinned[i] as in
  * ht_server_submit; pinned may be NULL for all-device requests) at
  * arrival_us[i] microseconds after the call starts (non-decreasing offsets;
- * the submitting thread spins on the clock between arrivals), writing its
- * digest to digests_host + i*k, then waits for all of them (bounded by
- * timeout_us after the last arrival).  A request the queue refuses (HT_ERR_BUSY)
- * is retried until it is admitted.  *late_us (if not NULL) receives the
- * largest delay between a request's scheduled arrival and its submission.
+ * the submitting thread spins on the clock and submits every request that
+ * is due at once), writing its digest to digests_host + i*k, then waits for
+ * all of them (each wait bounded by timeout_us).  A request's latency is
+ * counted from its scheduled arrival.  When the queue is full, due requests
+ * wait in the replay loop.  *late_us (if not NULL) receives the largest delay
+ * between a request's scheduled arrival and its submission.  Concurrent
+ * ht_server_submit calls during a replay are not allowed (tickets of the
+ * replay are consecutive).
  * Errors: HT_ERR_ARG, HT_ERR_BUDGET, HT_ERR_TIMEOUT, or the first failed
  * request's error. */
 int ht_server_replay(ht_server *srv, const void *const *ptrs, const uint64_t *lens,

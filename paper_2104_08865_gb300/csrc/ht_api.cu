@@ -524,6 +524,12 @@ static void batch_nodes(ht_ctx *c, const ht_shape &shape, cudaKernelNodeParams &
   nh.kernelParams = hargs;
 }
 
+// The general (unaligned-capable) batch kernel paired with the aligned-only
+// one of a shape (none for the stream kernel, which handles both).
+static const void *general_batch_kernel(const ht_ctx *c, const ht_shape &shape) {
+  return shape.kernel == 2 ? c->ks->range_batch_unaligned : c->ks->batch_unaligned[shape.chunk_levels - 1];
+}
+
 static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
@@ -536,11 +542,11 @@ static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
   HT_CUDA(cudaGraphCreate(&c->graph, 0));
   HT_CUDA(cudaGraphAddKernelNode(&c->node_plan, c->graph, nullptr, 0, &np));
   HT_CUDA(cudaGraphAddKernelNode(&c->node_hash, c->graph, &c->node_plan, 1, &nh));
-  if (shape.kernel == 2) {
+  if (shape.kernel != 0) {
     // the general (unaligned-capable) variant; the one the planner's flag
     // does not select returns at once
     cudaKernelNodeParams nu = nh;
-    nu.func = (void *)c->ks->range_batch_unaligned;
+    nu.func = (void *)general_batch_kernel(c, shape);
     HT_CUDA(cudaGraphAddKernelNode(&c->node_hash2, c->graph, &c->node_hash, 1, &nu));
   }
   HT_CUDA(cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
@@ -588,7 +594,7 @@ int ht_hash_batch(ht_ctx *c, const void *const *ptrs, const uint64_t *lens, size
     HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash, &nh));
     if (c->node_hash2) {
       cudaKernelNodeParams nu = nh;
-      nu.func = (void *)c->ks->range_batch_unaligned;
+      nu.func = (void *)general_batch_kernel(c, shape);
       HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash2, &nu));
     }
   }

@@ -90,7 +90,8 @@ struct PlanArgs {
 struct KernelSet {
   const void *single_aligned[3];    // [L-1]
   const void *single_unaligned[3];  // [L-1]
-  const void *batch[3];             // [L-1]
+  const void *batch[3];             // [L-1], aligned-only
+  const void *batch_unaligned[3];   // [L-1], general (see ctl.unaligned)
   const void *plan[4];              // [0]: stream, [L]: warp-chunk
   const void *stream_single;
   const void *stream_batch;

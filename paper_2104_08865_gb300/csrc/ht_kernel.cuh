@@ -445,13 +445,15 @@ __device__ __forceinline__ void exit_protocol(const KParams &P, int ln) {
 }
 
 template <int W, int L, bool SINGLE, bool ALIGNED>
-__global__ void __launch_bounds__(256) hash_kernel(const __grid_constant__ KParams P) {
+__global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KParams P) {
   const int ln = threadIdx.x & 31;
   uint64_t total;
   if (SINGLE) {
     total = P.item_end;
   } else {
-    if (__ldcg(&P.scr.ctl->status) != 0) {
+    // a batch runs an aligned-only and a general variant; the planner's
+    // alignment flag selects one, the other leaves at once
+    if (__ldcg(&P.scr.ctl->status) != 0 || (__ldcg(&P.scr.ctl->unaligned) != 0) == ALIGNED) {
       exit_protocol(P, ln);
       return;
     }
@@ -469,7 +471,7 @@ __global__ void __launch_bounds__(256) hash_kernel(const __grid_constant__ KPara
       const unsigned s = find_string(P.item0s, P.count, item);
       const StrPlan sp = P.plans[s];
       const uint64_t c = item - sp.item0;
-      if ((((uintptr_t)sp.ptr) & 15u) == 0)
+      if (ALIGNED || (((uintptr_t)sp.ptr) & 15u) == 0)
         hash_chunk<W, L, true>(P, sp, s, c, ln);
       else
         hash_chunk<W, L, false>(P, sp, s, c, ln);

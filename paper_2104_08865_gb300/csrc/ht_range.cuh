@@ -243,9 +243,12 @@ KernelSet make_kernel_set() {
   ks.single_unaligned[0] = (const void *)hash_kernel<W, 1, true, false>;
   ks.single_unaligned[1] = (const void *)hash_kernel<W, 2, true, false>;
   ks.single_unaligned[2] = (const void *)hash_kernel<W, 3, true, false>;
-  ks.batch[0] = (const void *)hash_kernel<W, 1, false, false>;
-  ks.batch[1] = (const void *)hash_kernel<W, 2, false, false>;
-  ks.batch[2] = (const void *)hash_kernel<W, 3, false, false>;
+  ks.batch[0] = (const void *)hash_kernel<W, 1, false, true>;
+  ks.batch[1] = (const void *)hash_kernel<W, 2, false, true>;
+  ks.batch[2] = (const void *)hash_kernel<W, 3, false, true>;
+  ks.batch_unaligned[0] = (const void *)hash_kernel<W, 1, false, false>;
+  ks.batch_unaligned[1] = (const void *)hash_kernel<W, 2, false, false>;
+  ks.batch_unaligned[2] = (const void *)hash_kernel<W, 3, false, false>;
   ks.plan[0] = (const void *)plan_kernel<W, 0>;
   ks.plan[1] = (const void *)plan_kernel<W, 1>;
   ks.plan[2] = (const void *)plan_kernel<W, 2>;

@@ -261,18 +261,47 @@ void dispatcher_main(ht_server *S) {
   }
 }
 
+// Retires batches.  Event queries run without the server lock (a busy,
+// launched slot is only touched by this thread until it is retired), so
+// submitters and the dispatcher are not held up while the GPU works.
 void completer_main(ht_server *S) {
   if (!S->fake && !S->slots.empty()) cudaSetDevice(S->slots[0].ctx->device);
-  std::unique_lock<std::mutex> lk(S->mu);
+  std::vector<size_t> watch, done;
+  std::vector<int> codes;
   for (;;) {
-    bool any_busy = false;
-    for (auto &sl : S->slots) {
-      if (!sl.busy) continue;
-      any_busy = true;
-      if (!sl.launched) continue;
-      const int rc = poll_slot(S, sl);
-      if (rc == 0) continue;
-      const int64_t t = now_ns();
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      watch.clear();
+      bool any_busy = false;
+      for (size_t i = 0; i < S->slots.size(); ++i)
+        if (S->slots[i].busy) {
+          any_busy = true;
+          if (S->slots[i].launched) watch.push_back(i);
+        }
+      if (S->stop && !any_busy) return;
+      if (watch.empty()) {
+        S->cv_complete.wait_for(lk, std::chrono::milliseconds(2));
+        continue;
+      }
+    }
+    done.clear();
+    codes.clear();
+    for (size_t i : watch) {
+      const int rc = poll_slot(S, S->slots[i]);
+      if (rc != 0) {
+        done.push_back(i);
+        codes.push_back(rc);
+      }
+    }
+    if (done.empty()) {
+      std::this_thread::yield();
+      continue;
+    }
+    const int64_t t = now_ns();
+    std::lock_guard<std::mutex> g(S->mu);
+    for (size_t d = 0; d < done.size(); ++d) {
+      Slot &sl = S->slots[done[d]];
+      const int rc = codes[d];
       for (size_t i = 0; i < sl.tickets.size(); ++i) {
         Req &r = S->reqs[sl.tickets[i]];
         if (rc == 1 && r.digest_host) memcpy(r.digest_host, sl.h_digests + i * S->k, S->k * sizeof(uint64_t));
@@ -292,17 +321,9 @@ void completer_main(ht_server *S) {
       sl.busy = false;
       sl.launched = false;
       sl.launch_status = HT_OK;
-      S->cv_dispatch.notify_all();
-      S->cv_done.notify_all();
     }
-    if (S->stop && !any_busy) break;
-    if (!any_busy) {
-      S->cv_complete.wait_for(lk, std::chrono::milliseconds(2));
-    } else {
-      lk.unlock();
-      std::this_thread::yield();
-      lk.lock();
-    }
+    S->cv_dispatch.notify_all();
+    S->cv_done.notify_all();
   }
 }
 
@@ -492,26 +513,40 @@ int ht_server_replay(ht_server *S, const void *const *ptrs, const uint64_t *lens
                      double *late_us) {
   if (!S || (n && (!ptrs || !lens || !arrival_us || !digests_host)))
     return ht::set_error(HT_ERR_ARG, "ht_server_replay: bad arguments");
-  std::vector<uint64_t> tickets(n);
+  for (size_t i = 0; i < n; ++i)
+    if (lens[i] > S->budget)
+      return ht::set_error(HT_ERR_BUDGET, "request %zu of %llu bytes exceeds the budget", i,
+                           (unsigned long long)lens[i]);
+  const size_t first = S->reqs.size();  // tickets are consecutive from here
   const int64_t t0 = now_ns();
   double worst = 0.0;
-  for (size_t i = 0; i < n; ++i) {
+  size_t i = 0;
+  while (i < n) {
     const int64_t due = t0 + (int64_t)(arrival_us[i] * 1000.0);
-    while (now_ns() < due) {
+    int64_t now = now_ns();
+    while (now < due) now = now_ns();
+    // every request due by now goes in under one lock acquisition
+    std::lock_guard<std::mutex> g(S->mu);
+    size_t j = i;
+    while (j < n && t0 + (int64_t)(arrival_us[j] * 1000.0) <= now && S->queue.size() < S->opts.max_queue) {
+      Req r;
+      r.ptr = ptrs[j];
+      r.len = lens[j];
+      r.pinned = pinned ? (pinned[j] ? 1 : 0) : 0;
+      r.digest_host = digests_host + j * (size_t)S->k;
+      r.t_arrive = t0 + (int64_t)(arrival_us[j] * 1000.0);  // scheduled arrival
+      S->reqs.push_back(r);
+      S->queue.push_back(S->reqs.size() - 1);
+      worst = std::max(worst, (now - r.t_arrive) / 1000.0);
+      ++j;
     }
-    for (;;) {
-      const int rc = ht_server_submit(S, ptrs[i], lens[i], pinned ? pinned[i] : 0,
-                                      digests_host + i * (size_t)S->k, &tickets[i]);
-      if (rc == HT_OK) break;
-      if (rc != HT_ERR_BUSY) return rc;
-      std::this_thread::yield();
-    }
-    worst = std::max(worst, (now_ns() - due) / 1000.0);
+    if (j > i) S->cv_dispatch.notify_one();
+    i = j;
   }
   if (late_us) *late_us = worst;
   int first_err = HT_OK;
-  for (size_t i = 0; i < n; ++i) {
-    const int rc = ht_server_wait(S, tickets[i], timeout_us);
+  for (size_t t = 0; t < n; ++t) {
+    const int rc = ht_server_wait(S, first + t, timeout_us);
     if (rc != HT_OK && first_err == HT_OK) first_err = rc;
   }
   return first_err;

@@ -210,9 +210,9 @@ def test_launch_counter_counts_kernels(dev):
     torch.cuda.synchronize()
     from paper_2104_08865_gb300 import abi
     batch_kernel = abi.ht_get_shape(h.ctx, 2**64 - 1)["kernel"]
-    # one hash kernel, then the planner and the batch kernel (the hybrid
-    # family runs an aligned and a general batch kernel)
-    assert h.launches() - before == 1 + (3 if batch_kernel == 2 else 2)
+    # one hash kernel, then the planner and the batch kernels (an aligned
+    # and a general one, except for the stream family)
+    assert h.launches() - before == 1 + (2 if batch_kernel == 0 else 3)
 
 
 @pytest.mark.parametrize("width", WIDTHS)
