@@ -109,6 +109,65 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def _profiled_traffic(width, nbytes, shape):
+    """DRAM bytes per launch from profiles/traffic.json, only while the kernel
+    sources are those that were profiled and the launch is the profiled one
+    (1 GiB, warp-chunk kernel with 64-execution chunks)."""
+    import hashlib
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        h = hashlib.sha256()
+        for f in t["kernel_sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != t["kernel_sources_sha256"]:
+            return None
+        if nbytes != GIB or shape.get("kernel") != 1 or shape.get("chunk_levels") != 2:
+            return None
+        return t["bytes_per_launch"].get(str(width))
+    except Exception:
+        return None
+
+
+def run_size_sweep(args):
+    """Per-launch time of one width over string sizes 1 MiB .. 4 GiB (CUDA
+    events, back-to-back launches): separates the fixed cost of a launch from
+    the steady-state bandwidth."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2104_08865_gb300 import Hasher, abi, inputs
+    dev = torch.device("cuda", 0)
+    maxn = 4 * GIB
+    data = inputs.stream_bytes_torch(SEED_DATA, 0, maxn, dev)
+    out = torch.empty(5, dtype=torch.int64, device=dev)
+    s = torch.cuda.current_stream()
+    rows = []
+    for w in args.sweep_widths:
+        h = Hasher(w, seed_words=abi.ht_seed_expand(SEED_KEY, w))
+        for n in [1 << 20, 16 << 20, 64 << 20, 256 << 20, 512 << 20, GIB, 2 * GIB, 4 * GIB]:
+            reps = max(5, min(200, (8 * GIB) // n))
+            for _ in range(3):
+                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), s)
+            e1.record(s)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1000 / reps
+            rows.append({"width": w, "bytes": n, "us": round(us, 2), "gbs": round(n / us / 1e3, 1)})
+        h.close()
+    fits = {}
+    for w in args.sweep_widths:
+        a = [r for r in rows if r["width"] == w and r["bytes"] in (2 * GIB, 4 * GIB)]
+        slope = (a[1]["us"] - a[0]["us"]) / (a[1]["bytes"] - a[0]["bytes"])  # us per byte
+        fits[str(w)] = {"steady_gbs": round(1 / slope / 1e3, 1),
+                        "fixed_us": round(a[1]["us"] - slope * a[1]["bytes"], 1)}
+    print(json.dumps({"size_sweep": rows, "fit_2_to_4_gib": fits}), flush=True)
+    return 0
+
+
 def _oracle_gbs(data_np, n_bytes: int):
     """The oracle over the first n_bytes at every width, one thread per width."""
     import numpy as np
@@ -360,13 +419,7 @@ def run_gpu(args):
     dom = max(WIDTHS, key=lambda w: per_w[w])
     peak, peak_kind = _peaks()
     achieved = nbytes / (per_w[dom] / 1e3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath) and nbytes == GIB:
-        try:
-            traffic = json.load(open(tpath)).get(str(dom))
-        except Exception:
-            traffic = None
+    traffic = _profiled_traffic(dom, nbytes, shapes.get(str(dom), {}))
     digests = {w: outs[w].cpu().numpy().view(np.uint64).tolist() for w in WIDTHS}
 
     # ---- end to end: pinned host input through ht_hash_host ---------------
@@ -455,6 +508,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-bytes", type=int, default=GIB)
+    ap.add_argument("--size-sweep", action="store_true",
+                    help="print per-launch times over string sizes instead of the benchmark line")
+    ap.add_argument("--sweep-widths", type=lambda v: [int(x) for x in v.split(",")], default=[24, 40])
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-strings", type=int, default=50_000)
     ap.add_argument("--no-serve", action="store_true")
@@ -467,6 +523,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.size_sweep:
+        return run_size_sweep(args)
     return run_gpu(args)
 
 
