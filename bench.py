@@ -383,6 +383,24 @@ def run_gpu(args):
             if evs is not None:
                 evs[i][1].record(stream)
 
+    # per-launch times for the roofline: each launch alone, bracketed by events
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    solo = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+             for _ in WIDTHS] for _ in range(max(3, min(args.steps, 50)))]
+    for ev in solo:
+        step(ev)
+    torch.cuda.synchronize()
+    per_w = {}
+    for i, w in enumerate(WIDTHS):
+        per_w[w] = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for ev in solo)
+    # the timed step: the four launches back to back; with overlap on, each
+    # launch may start while the previous one drains (its input is never the
+    # previous launch's output)
+    if not args.no_overlap:
+        for w in WIDTHS:
+            abi.ht_ctx_set_flags(hashers[w].ctx, abi.HT_FLAG_OVERLAP_LAUNCHES)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -392,14 +410,12 @@ def run_gpu(args):
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
-    per = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-            for _ in WIDTHS] for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t_start.record(stream)
     for s in range(args.steps):
-        step(per[s])
+        step()
     t_end.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
@@ -412,10 +428,6 @@ def run_gpu(args):
     ms_step = ms_total / args.steps
     total_bytes = ws * args.steps * len(WIDTHS) * nbytes
     value = total_bytes / (ms_total / 1e3) / 1e9
-    per_w = {}
-    for i, w in enumerate(WIDTHS):
-        ms = [per[s][i][0].elapsed_time(per[s][i][1]) for s in range(args.steps)]
-        per_w[w] = statistics.mean(ms)
     dom = max(WIDTHS, key=lambda w: per_w[w])
     peak, peak_kind = _peaks()
     achieved = nbytes / (per_w[dom] / 1e3) / 1e9
@@ -476,8 +488,11 @@ def run_gpu(args):
                                    "at widths 16/24/32/40 (seed %d) per step" % (nbytes >> 20, SEED_DATA, SEED_KEY),
                        "bytes_per_step": len(WIDTHS) * nbytes,
                        "l2": "inputs larger than L2 (no flush)",
+                       "launches": "back to back on one stream" + (
+                           "" if args.no_overlap else ", overlapping (programmatic dependent launch)"),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "per_width_gbs": {str(w): round(nbytes / (per_w[w] / 1e3) / 1e9, 2) for w in WIDTHS},
+            "per_width_note": "each launch alone, bracketed by CUDA events (no overlap)",
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "%s<%d> (single string)" % (
@@ -511,6 +526,8 @@ def main():
     ap.add_argument("--size-sweep", action="store_true",
                     help="print per-launch times over string sizes instead of the benchmark line")
     ap.add_argument("--sweep-widths", type=lambda v: [int(x) for x in v.split(",")], default=[24, 40])
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="time the step without overlapping consecutive launches")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-strings", type=int, default=50_000)
     ap.add_argument("--no-serve", action="store_true")

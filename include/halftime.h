@@ -88,6 +88,19 @@ int ht_ctx_destroy(ht_ctx *ctx);
 int ht_ctx_rekey(ht_ctx *ctx, const uint64_t *seed_words_host, size_t n_words,
                  ht_stream_t stream);
 
+/* Context flags.
+ * HT_FLAG_OVERLAP_LAUNCHES: single-string launches of this context may start
+ *   while the kernel before them in the stream is still finishing
+ *   (programmatic dependent launch): each warp hashes its first chunk of the
+ *   input before waiting for that kernel.  Safe only when the input of a call
+ *   is never written by the kernel launched just before it (for example, not
+ *   the digest buffer of the previous call); the context's own scratch is
+ *   always protected.  Hides most of the fixed start and end cost of
+ *   back-to-back hashes.  Default: off.
+ * Errors: HT_ERR_ARG (unknown flag). */
+#define HT_FLAG_OVERLAP_LAUNCHES 1u
+int ht_ctx_set_flags(ht_ctx *ctx, unsigned flags);
+
 /* Reserves device scratch so that ht_hash_batch can take up to max_strings
  * strings whose lengths add up to at most max_total_bytes (the default after
  * ht_ctx_create is 65536 strings and 16 GiB).  Synchronises the device.

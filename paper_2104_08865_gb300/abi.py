@@ -77,6 +77,7 @@ _PROTOS = {
     "ht_ctx_reserve": (_int, [_vp, _u64, _sz]),
     "ht_ctx_rekey": (_int, [_vp, _u64p, _sz, _vp]),
     "ht_ctx_status": (_int, [_vp, _vp]),
+    "ht_ctx_set_flags": (_int, [_vp, ctypes.c_uint]),
     "ht_hash": (_int, [_vp, _vp, _u64, _vp, _vp]),
     "ht_hash_host": (_int, [_vp, _vp, _u64, _vp, _vp]),
     "ht_hash_batch": (_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
@@ -189,6 +190,13 @@ def ht_ctx_rekey(ctx: int, seed_words, stream=None) -> None:
 
 def ht_ctx_reserve(ctx: int, max_total_bytes: int, max_strings: int) -> None:
     _check(_lib.ht_ctx_reserve(ctx, max_total_bytes, max_strings))
+
+
+HT_FLAG_OVERLAP_LAUNCHES = 1
+
+
+def ht_ctx_set_flags(ctx: int, flags: int) -> None:
+    _check(_lib.ht_ctx_set_flags(ctx, flags))
 
 
 def ht_ctx_status(ctx: int, stream=None) -> None:

@@ -269,7 +269,23 @@ int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t 
   P.total_warps = (unsigned)(grid * wpb);
   P.stages = (unsigned)shape.stages;
   void *args[] = {&P};
-  HT_CUDA(cudaLaunchKernel(func, dim3((unsigned)grid), dim3(tpb), args, smem, s));
+  if (shape.kernel == 1 && (c->flags & HT_FLAG_OVERLAP_LAUNCHES)) {
+    // programmatic dependent launch: may start while the previous kernel of
+    // the stream drains; the kernel waits before touching its scratch
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(tpb);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    HT_CUDA(cudaLaunchKernelExC(&cfg, func, args));
+  } else {
+    HT_CUDA(cudaLaunchKernel(func, dim3((unsigned)grid), dim3(tpb), args, smem, s));
+  }
   c->launches.fetch_add(1);
   return HT_OK;
 }
@@ -612,6 +628,13 @@ int ht_hash_batch_naive(ht_ctx *c, const void *const *ptrs_host, const uint64_t 
     int rc = ht_hash(c, ptrs_host[i], lens_host[i], digests + i * (size_t)k, stream);
     if (rc) return rc;
   }
+  return HT_OK;
+}
+
+int ht_ctx_set_flags(ht_ctx *c, unsigned flags) {
+  if (!c || (flags & ~(unsigned)HT_FLAG_OVERLAP_LAUNCHES))
+    return set_error(HT_ERR_ARG, "ht_ctx_set_flags: unknown flags %u", flags);
+  c->flags = flags;
   return HT_OK;
 }
 

@@ -57,6 +57,15 @@ __device__ __forceinline__ uint64_t ld_cg(const unsigned long long *p) {
   return __ldcg(p);
 }
 
+// Programmatic dependent launch: a launch that the host marked as allowed to
+// overlap its predecessor in the stream waits here for that predecessor to
+// finish (and its writes to be visible); without the mark this returns at once.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next launch in the stream start as soon as SM resources free up.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---- loads ----------------------------------------------------------------------
 
 // 16 bytes of input read once: no L1 allocation.
@@ -342,6 +351,9 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
       }
     }
 
+    // everything below touches the context's scratch: an overlapping launch
+    // must first see its predecessor finish
+    griddep_wait();
     if (full) {
       // climb from the chunk root (level L, index c); thread x owns tree x
       uint64_t v0 = 0, v1 = 0;
@@ -402,6 +414,7 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
     }
   }
 
+  griddep_wait();
   if (__any_sync(kFull, anyp)) {
 #pragma unroll
     for (int t = 0; t < k; ++t) pend[t] = warp_sum(pend[t]);
@@ -431,6 +444,7 @@ __device__ __forceinline__ unsigned find_string(const unsigned long long *item0s
 }
 
 __device__ __forceinline__ void exit_protocol(const KParams &P, int ln) {
+  griddep_wait();
   __syncwarp();
   if (ln == 0) {
     __threadfence();
@@ -459,11 +473,22 @@ __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KP
     }
     total = __ldcg(&P.scr.ctl->total);
   }
+  // single string: each warp's first chunk is fixed (chunk = warp index), so
+  // it can be hashed before the scratch may be touched; later chunks come
+  // from the cursor
+  if (SINGLE) griddep_launch_dependents();
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  bool first = SINGLE;
   for (;;) {
     unsigned long long item = 0;
-    if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
-    item = __shfl_sync(kFull, item, 0);
-    if (SINGLE) item += P.item_begin;
+    if (first) {
+      item = P.item_begin + gw;
+      first = false;
+    } else {
+      if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
+      item = __shfl_sync(kFull, item, 0);
+      if (SINGLE) item += P.item_begin + P.total_warps;
+    }
     if (item >= total) break;
     if (SINGLE) {
       hash_chunk<W, L, ALIGNED>(P, P.single, 0, item, ln);

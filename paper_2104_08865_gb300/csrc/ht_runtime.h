@@ -17,6 +17,7 @@ struct ht_ctx {
   int device = 0;
   int num_sms = 1;
   int smem_optin = 0;  // max dynamic shared memory per block
+  unsigned flags = 0;  // HT_FLAG_*
   const ht::KernelSet *ks = nullptr;
   std::vector<uint64_t> h_seeds;
   unsigned long long *d_seeds = nullptr;

@@ -226,6 +226,45 @@ def test_rekey_matches_fresh_context(dev, width):
     assert np.array_equal(got, oracle.hash_bytes(width, ref2, data))
 
 
+def test_overlapped_launches_keep_digests(dev):
+    """Back-to-back hashes with HT_FLAG_OVERLAP_LAUNCHES (each launch may
+    start while the previous one drains) on two contexts sharing one stream,
+    over sizes from empty to several rounds of chunks: every digest equals the
+    oracle's."""
+    from paper_2104_08865_gb300 import abi
+    pairs = [_pair(24, seed=3), _pair(40, seed=4)]
+    for h, _ in pairs:
+        abi.ht_ctx_set_flags(h.ctx, abi.HT_FLAG_OVERLAP_LAUNCHES)
+    lens = [0, 17, 5000, 300_000, 9 << 20, (1 << 26) + 12345, 3 << 20, 1 << 27]
+    data = inputs.stream_bytes_torch(15, 0, max(lens), dev)
+    outs = []
+    for rep in range(2):
+        for n in lens:
+            for h, _ in pairs:
+                outs.append((h, n, h.hash(data, n)))  # no synchronisation in between
+    torch.cuda.synchronize()
+    host = data.cpu().numpy()
+    want = {}
+    for h, ref in pairs:
+        for n in lens:
+            want[(h.width, n)] = oracle.hash_bytes(h.width, ref, host[:n])
+    for h, n, got in outs:
+        assert np.array_equal(_u64(got), want[(h.width, n)]), (h.width, n)
+
+
+def test_default_launches_hash_the_previous_digest(dev):
+    """Without the overlap flag a call may hash what the previous call wrote:
+    the digest of a string, hashed again, equals the oracle's chain."""
+    h, ref = _pair(32)
+    data = inputs.stream_bytes_torch(16, 0, 50 << 20, dev)
+    d1 = h.hash(data)
+    d2 = h.hash(d1.view(torch.uint8))
+    want1 = oracle.hash_bytes(32, ref, data.cpu().numpy())
+    want2 = oracle.hash_bytes(32, ref, want1.view(np.uint8))
+    assert np.array_equal(_u64(d1), want1)
+    assert np.array_equal(_u64(d2), want2)
+
+
 def test_serving_alone_vs_mix(dev):
     """Requests of mixed sizes (device-resident and pinned host) arrive while
     others are on the GPU; every digest equals the one hashed alone, and the
