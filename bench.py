@@ -238,9 +238,13 @@ def run_batch(args, dev, stream):
     import numpy as np
     import torch
 
-    from paper_2104_08865_gb300 import Hasher, abi, inputs
-    count = args.batch_strings
-    lens = inputs.log_uniform_lengths(3, count, 64, 1 << 20)
+    from paper_2104_08865_gb300 import Hasher, abi, inputs, shard
+    ws, rank, _ = _dist()
+    all_lens = inputs.log_uniform_lengths(3, args.batch_strings, 64, 1 << 20)
+    # under torchrun each rank hashes a byte-balanced, contiguous share
+    lo, hi = shard.shard_of(all_lens, ws, rank)
+    lens = all_lens[lo:hi]
+    count = len(lens)
     offs, total = _aligned_offsets(lens)
     buf = inputs.stream_bytes_torch(3, 0, total + 256, dev)
     ptrs = torch.tensor(buf.data_ptr() + offs, dtype=torch.int64, device=dev)
@@ -259,9 +263,9 @@ def run_batch(args, dev, stream):
         abi.ht_hash_batch(h.ctx, ptrs, lt, count, out, stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_batch = e0.elapsed_time(e1) / reps
+    ms_batch = shard.max_over_ranks(e0.elapsed_time(e1) / reps, dev)
     launches_batch = (h.launches() - l0) // reps
-    nbytes = int(lens.sum())
+    nbytes = int(all_lens.sum())
     naive = torch.empty_like(out)
     hp = (buf.data_ptr() + offs).astype(np.uint64)
     h.hash_batch_naive(hp, lens, naive)  # warm-up
@@ -270,14 +274,15 @@ def run_batch(args, dev, stream):
     h.hash_batch_naive(hp, lens, naive)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_naive = e0.elapsed_time(e1)
+    ms_naive = shard.max_over_ranks(e0.elapsed_time(e1), dev)
     same = bool(torch.equal(out, naive))
     h.close()
-    return {"workload": "%d strings, log-uniform 64 B..1 MiB, %.2f GB, width 24" % (count, nbytes / 1e9),
+    return {"workload": "%d strings, log-uniform 64 B..1 MiB, %.2f GB, width 24%s" % (
+                args.batch_strings, nbytes / 1e9, "" if ws == 1 else ", sharded by bytes over %d ranks" % ws),
             "batch_gbs": round(nbytes / ms_batch / 1e6, 1), "batch_ms": round(ms_batch, 3),
             "batch_launches": launches_batch,
             "naive_gbs": round(nbytes / ms_naive / 1e6, 1), "naive_ms": round(ms_naive, 3),
-            "naive_launches": count, "speedup": round(ms_naive / ms_batch, 2),
+            "naive_launches": args.batch_strings, "speedup": round(ms_naive / ms_batch, 2),
             "digests_equal": same}
 
 
@@ -475,7 +480,7 @@ def run_gpu(args):
                          "per width (%.1f s)" % (sample >> 20, dt),
                "digests_match_gpu": match}
 
-    batch = run_batch(args, dev, stream) if (rank == 0 and not args.no_batch) else None
+    batch = run_batch(args, dev, stream) if not args.no_batch else None
     serving = run_serving(args, dev, stream) if (rank == 0 and not args.no_serve) else None
 
     if rank == 0:
