@@ -159,6 +159,59 @@ int ht_hash_batch_naive(ht_ctx *ctx, const void *const *ptrs_host,
                         const uint64_t *lens_host, size_t count,
                         uint64_t *digests_dev, ht_stream_t stream);
 
+/* ---- one string in parts (on several devices, or several launches) -------
+ * A long string can be split at multiples of ht_part_granule(ctx) bytes (one
+ * 64-execution chunk) and its parts hashed independently, each into the
+ * "part state" of its own context (same width and seed; for example one
+ * context per GPU).  A part state is an array of 64-bit words in which every
+ * entry is a sum of contributions, so the states of all parts combine by
+ * element-wise addition mod 2^64 — one all-reduce (sum, uint64) across
+ * devices, or ht_part_merge on one device.  ht_finish_parts then completes
+ * the tree groups whose children were split between parts and writes the
+ * digest (Section 5.2 tree levels, Section 6.1 finaliser); the part that ends
+ * the string has already added the tail, so finishing reads no input.
+ * Sequence per context: ht_part_begin, ht_hash_part (any number of parts),
+ * then either export the state (ht_part_state) or receive the others'
+ * (ht_part_merge) and ht_finish_parts on one of them.  Calls on a context are
+ * stream-ordered like the others. */
+
+/* Bytes per split unit: parts start and end on multiples of this. */
+uint64_t ht_part_granule(ht_ctx *ctx);
+
+/* Size in 64-bit words of the part state of a string of total_len bytes. */
+size_t ht_part_state_words(ht_ctx *ctx, uint64_t total_len);
+
+/* Opens (and zeroes, on `stream`) the part state for a string of total_len
+ * bytes.  state_dev: a device buffer of at least ht_part_state_words words
+ * that the caller owns and keeps alive until ht_finish_parts (for example a
+ * tensor it will all-reduce), or NULL for a buffer the context allocates.
+ * Errors: HT_ERR_ARG (buffer too small), HT_ERR_NOMEM, HT_ERR_CUDA. */
+int ht_part_begin(ht_ctx *ctx, uint64_t total_len, void *state_dev, size_t words,
+                  ht_stream_t stream);
+
+/* Hashes bytes [part_offset, part_offset + part_len) of the string into the
+ * part state; part_dev points at the part's first byte (device).  part_offset
+ * and, unless the part ends the string, part_len must be multiples of the
+ * granule.  Errors: HT_ERR_ARG (no open state, misaligned or out-of-range
+ * part), HT_ERR_CUDA. */
+int ht_hash_part(ht_ctx *ctx, const void *part_dev, uint64_t part_offset,
+                 uint64_t part_len, ht_stream_t stream);
+
+/* The open part state: *state_dev (device array owned by the context) and
+ * its size in 64-bit words, for exchanging it with other devices.
+ * Errors: HT_ERR_ARG. */
+int ht_part_state(ht_ctx *ctx, void **state_dev, size_t *words);
+
+/* Adds another part state of the same string (a device array of `words`
+ * 64-bit words on this context's device) into this context's state.
+ * Errors: HT_ERR_ARG (size mismatch), HT_ERR_CUDA. */
+int ht_part_merge(ht_ctx *ctx, const void *state_dev, size_t words,
+                  ht_stream_t stream);
+
+/* Completes the merged state and writes the k digest words to digest_dev;
+ * closes the state.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_finish_parts(ht_ctx *ctx, uint64_t *digest_dev, ht_stream_t stream);
+
 /* ---- hashing without allocation ---------------------------------------------
  * (The paper has no counterpart: this serves deployments, not the method.)
  * Some callers cannot allocate device memory: code running inside another

@@ -83,6 +83,13 @@ _PROTOS = {
     "ht_hash_batch": (_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "ht_hash_batch_naive": (_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "ht_hash_noalloc": (_int, [_int, _u64p, _sz, _vp, _u64, _vp, _vp]),
+    "ht_part_granule": (_u64, [_vp]),
+    "ht_part_state_words": (_sz, [_vp, _u64]),
+    "ht_part_begin": (_int, [_vp, _u64, _vp, _sz, _vp]),
+    "ht_hash_part": (_int, [_vp, _vp, _u64, _u64, _vp]),
+    "ht_part_state": (_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_sz)]),
+    "ht_part_merge": (_int, [_vp, _vp, _sz, _vp]),
+    "ht_finish_parts": (_int, [_vp, _vp, _vp]),
     "ht_autotune": (_int, [_vp, _u64, _vp, ctypes.POINTER(ht_shape)]),
     "ht_get_shape": (_int, [_vp, _u64, ctypes.POINTER(ht_shape)]),
     "ht_set_shape": (_int, [_vp, _u64, ctypes.POINTER(ht_shape)]),
@@ -227,6 +234,38 @@ def ht_hash_noalloc(width: int, seed_words, data_dev, length: int, digest_dev, s
     seed_words = np.ascontiguousarray(seed_words, dtype=np.uint64)
     _check(_lib.ht_hash_noalloc(width, seed_words.ctypes.data_as(_u64p), seed_words.size,
                                 _ptr(data_dev), length, _ptr(digest_dev), _stream(stream)))
+
+
+def ht_part_granule(ctx: int) -> int:
+    return int(_lib.ht_part_granule(ctx))
+
+
+def ht_part_state_words(ctx: int, total_len: int) -> int:
+    return int(_lib.ht_part_state_words(ctx, total_len))
+
+
+def ht_part_begin(ctx: int, total_len: int, state_dev=None, words: int = 0, stream=None) -> None:
+    _check(_lib.ht_part_begin(ctx, total_len, _ptr(state_dev), words, _stream(stream)))
+
+
+def ht_hash_part(ctx: int, part_dev, part_offset: int, part_len: int, stream=None) -> None:
+    _check(_lib.ht_hash_part(ctx, _ptr(part_dev), part_offset, part_len, _stream(stream)))
+
+
+def ht_part_state(ctx: int):
+    """(device pointer, words) of the open part state."""
+    p = _vp()
+    n = _sz()
+    _check(_lib.ht_part_state(ctx, ctypes.byref(p), ctypes.byref(n)))
+    return p.value, n.value
+
+
+def ht_part_merge(ctx: int, state_dev, words: int, stream=None) -> None:
+    _check(_lib.ht_part_merge(ctx, _ptr(state_dev), words, _stream(stream)))
+
+
+def ht_finish_parts(ctx: int, digest_dev, stream=None) -> None:
+    _check(_lib.ht_finish_parts(ctx, _ptr(digest_dev), _stream(stream)))
 
 
 def ht_autotune(ctx: int, length: int, stream=None) -> dict:

@@ -381,6 +381,7 @@ int ht_ctx_destroy(ht_ctx *c) {
     if (c->ev_hash[i]) cudaEventDestroy(c->ev_hash[i]);
   }
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->part_owned) cudaFree(c->part_buf);
   delete c;
   return HT_OK;
 }

@@ -99,6 +99,8 @@ struct KernelSet {
   const void *range_single_unaligned;
   const void *range_batch;   // [aligned-only, general] pair, see ctl.unaligned
   const void *range_batch_unaligned;
+  const void *part_tail;    // parts: tail NH of the last part
+  const void *part_finish;  // parts: climb merged groups, write the digest
   int exec_bytes, k, n_seed, off_T, off_F, off_R, ew;
 };
 

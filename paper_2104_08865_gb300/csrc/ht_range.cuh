@@ -14,6 +14,7 @@
 // as in the stream kernel.
 #pragma once
 
+#include "ht_parts.cuh"
 #include "ht_stream.cuh"
 
 namespace ht {
@@ -259,6 +260,8 @@ KernelSet make_kernel_set() {
   ks.range_single_unaligned = (const void *)range_kernel<W, false, false>;
   ks.range_batch = (const void *)range_kernel<W, true, true>;
   ks.range_batch_unaligned = (const void *)range_kernel<W, true, false>;
+  ks.part_tail = (const void *)part_tail_kernel<W>;
+  ks.part_finish = (const void *)part_finish_kernel<W, 2>;
   ks.exec_bytes = Dims<W>::exec_bytes;
   ks.k = Spec<W>::k;
   ks.n_seed = Dims<W>::n_seed;

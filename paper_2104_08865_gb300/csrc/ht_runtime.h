@@ -49,6 +49,11 @@ struct ht_ctx {
   uint64_t stage_bytes = 0;
   cudaEvent_t ev_copy[kStageSlots] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_hash[kStageSlots] = {nullptr, nullptr, nullptr, nullptr};
+  // one string in parts (ht_part_*)
+  unsigned long long *part_buf = nullptr;
+  uint64_t part_cap_words = 0, part_len = 0;
+  bool part_open = false;
+  bool part_owned = false;  // part_buf allocated by the library
   std::atomic<uint64_t> launches{0};
 };
 

@@ -59,3 +59,39 @@ def gather_digests(local: np.ndarray, counts, device=None) -> np.ndarray:
     dist.all_gather(parts, t)
     rows = [p.cpu().numpy().view(np.uint64)[:int(c)] for p, c in zip(parts, counts)]
     return np.concatenate(rows, axis=0)
+
+
+def part_bounds(total_len: int, granule: int, world: int):
+    """Byte boundaries of `world` parts of one string: multiples of the
+    granule, about equal, the last one ending at total_len."""
+    units = -(-total_len // granule) if total_len else 0
+    b = [min(total_len, (units * r // world) * granule) for r in range(world)] + [total_len]
+    return b
+
+
+def hash_split(hasher, data, total_len: int, world: int, rank: int, device=None):
+    """Hashes one string split across the ranks of the process group: rank r
+    hashes part r of `data` (a CUDA uint8 tensor holding the whole string,
+    or at least part r at its offset) into a state tensor, the states are
+    summed with one all-reduce, and every rank finishes the same digest.
+    Returns the digest as a uint64 numpy array."""
+    import torch
+    import torch.distributed as dist
+
+    from . import abi
+    dev = device if device is not None else data.device
+    words = abi.ht_part_state_words(hasher.ctx, total_len)
+    state = torch.zeros(words, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    abi.ht_part_begin(hasher.ctx, total_len, state.data_ptr(), words, stream)
+    b = part_bounds(total_len, abi.ht_part_granule(hasher.ctx), world)
+    lo, hi = b[rank], b[rank + 1]
+    if hi > lo or hi == total_len:
+        abi.ht_hash_part(hasher.ctx, data.data_ptr() + lo, lo, hi - lo, stream)
+    torch.cuda.synchronize(dev)
+    if dist.is_available() and dist.is_initialized() and world > 1:
+        dist.all_reduce(state, op=dist.ReduceOp.SUM)  # int64 sums wrap like uint64
+    out = torch.empty(hasher.k, dtype=torch.int64, device=dev)
+    abi.ht_finish_parts(hasher.ctx, out.data_ptr(), stream)
+    torch.cuda.synchronize(dev)
+    return out.cpu().numpy().view(np.uint64)
