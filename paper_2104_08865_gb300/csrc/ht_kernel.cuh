@@ -114,6 +114,52 @@ __device__ __forceinline__ uint64_t tail_word(const uint8_t *p, uint32_t nb) {
   return w;
 }
 
+// Row t of Combine, y_t = sum_c T[t][c] * h_c mod 2^64 (Section 5.1), as
+// sum_c T*lo(h_c) + 2^32 * sum_c T*hi(h_c): a 64-bit multiply-add of the low
+// halves (mad.wide.u32) and a 32-bit one of the high halves per nonzero
+// coefficient, whatever the coefficient.
+__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+  uint64_t d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+template <class S, int E>
+__device__ __forceinline__ uint64_t combine_row_mad(int t, const uint64_t (&h)[E]) {
+  uint64_t lo = 0;
+  uint32_t hi = 0;
+#pragma unroll
+  for (int c = 0; c < E; ++c) {
+    const uint32_t coef = (uint32_t)S::T(t, c);
+    if (coef != 0) {
+      lo = mad_wide(coef, (uint32_t)h[c], lo);
+      hi += coef * (uint32_t)(h[c] >> 32);
+    }
+  }
+  return lo + ((uint64_t)hi << 32);
+}
+
+// The same row as plain 64-bit arithmetic (the compiler picks shifts, adds
+// and multiplies per coefficient).
+template <class S, int E>
+__device__ __forceinline__ uint64_t combine_row_plain(int t, const uint64_t (&h)[E]) {
+  uint64_t acc = 0;
+#pragma unroll
+  for (int c = 0; c < E; ++c) {
+    if (S::T(t, c) == 1) acc += h[c];
+    else if (S::T(t, c) != 0) acc += (uint64_t)S::T(t, c) * h[c];
+  }
+  return acc;
+}
+
+// Measured on GB300: the split form is faster for width 32 (about 2%), the
+// plain form for width 40; both are equal for widths 16 and 24.
+template <int W, int E>
+__device__ __forceinline__ uint64_t combine(int t, const uint64_t (&h)[E]) {
+  if constexpr (W == 32) return combine_row_mad<Spec<W>>(t, h);
+  else return combine_row_plain<Spec<W>>(t, h);
+}
+
 // ---- EHC ------------------------------------------------------------------------
 
 // One EHC execution for block lanes 2p and 2p+1 (Section 3.3, Section 5.1):
@@ -160,15 +206,7 @@ __device__ __forceinline__ void ehc2(const uint8_t *ex, int p, uint32_t sh,
       }
     }
 #pragma unroll
-    for (int t = 0; t < k; ++t) {
-      uint64_t acc = 0;
-#pragma unroll
-      for (int c = 0; c < e; ++c) {
-        if (S::T(t, c) == 1) acc += h[c];
-        else if (S::T(t, c) != 0) acc += (uint64_t)S::T(t, c) * h[c];
-      }
-      y[l][t] = acc;
-    }
+    for (int t = 0; t < k; ++t) y[l][t] = combine<W>(t, h);
   }
 }
 

@@ -111,15 +111,7 @@ __device__ __forceinline__ void ehc2_from(Ld ld, const KParams &P, uint64_t (&y)
       }
     }
 #pragma unroll
-    for (int t = 0; t < k; ++t) {
-      uint64_t acc = 0;
-#pragma unroll
-      for (int c = 0; c < e; ++c) {
-        if (S::T(t, c) == 1) acc += h[c];
-        else if (S::T(t, c) != 0) acc += (uint64_t)S::T(t, c) * h[c];
-      }
-      y[l][t] = acc;
-    }
+    for (int t = 0; t < k; ++t) y[l][t] = combine<W>(t, h);
   }
 }
 
