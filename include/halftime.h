@@ -36,6 +36,7 @@ extern "C" {
 typedef struct CUstream_st *ht_stream_t; /* same type as cudaStream_t */
 typedef struct ht_ctx ht_ctx;
 typedef struct ht_server ht_server;
+typedef struct ht_inc ht_inc;
 
 /* ---- status codes -------------------------------------------------------- */
 #define HT_OK 0
@@ -211,6 +212,75 @@ int ht_part_merge(ht_ctx *ctx, const void *state_dev, size_t words,
 /* Completes the merged state and writes the k digest words to digest_dev;
  * closes the state.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
 int ht_finish_parts(ht_ctx *ctx, uint64_t *digest_dev, ht_stream_t stream);
+
+/* ---- incremental hashing: init / update / final ------------------------------
+ * A string that arrives in pieces of any length, one after another, with its
+ * total length unknown until the end (a file read in blocks, a network
+ * stream, data larger than device memory).  The handle carries the string's
+ * eager tree counter between calls (Section 5.2: for every level, the
+ * pending nodes of its last, incomplete group, one value per tree and lane,
+ * on a stack) plus a buffer of up to one 64-execution chunk of bytes.
+ * Updates hash whole chunks straight from the caller's memory; only bytes
+ * that straddle an update boundary are copied.  ht_inc_final hashes the
+ * stack's pending nodes with their final keys, the buffered executions and
+ * the tail (Section 6.1).  The digest equals ht_hash of the concatenation of
+ * all pieces, for any way of cutting it.
+ *   - A handle belongs to one context (its width and seed words) and must not
+ *     outlive it; rekeying the context while a string is open gives a
+ *     meaningless digest.
+ *   - Calls on one handle are stream-ordered: issue them on one stream (or
+ *     order the streams); one handle is not for concurrent host threads.
+ *     Different handles are independent (each has its own scratch).
+ *   - The state can be saved to host memory and restored into another
+ *     handle of a context with the same width and seed words, in this or
+ *     another process, to resume the string later. */
+
+/* Creates a handle (1.3 to 3.1 MB of device memory by width; host updates add
+ * two staging slots of 1024 chunks) with an open, empty string.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_inc_create(ht_ctx *ctx, ht_inc **out);
+int ht_inc_destroy(ht_inc *h);
+
+/* Starts a new, empty string (clears the handle's scratch on `stream`).
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_inc_init(ht_inc *h, ht_stream_t stream);
+
+/* Appends len bytes at data_dev (device, any alignment) to the string.
+ * Asynchronous: data_dev must stay valid until `stream` reaches this point.
+ * Errors: HT_ERR_ARG (no open string, NULL data), HT_ERR_TOO_LONG (total
+ * length would exceed 2^64 - 1), HT_ERR_CUDA. */
+int ht_inc_update(ht_inc *h, const void *data_dev, uint64_t len, ht_stream_t stream);
+
+/* As ht_inc_update for bytes in HOST memory (pinned for full speed): whole
+ * chunks are copied in pieces of 1024 chunks through two device slots on a
+ * copy stream, each copy overlapping the hashing of the previous piece.
+ * Returns once every byte has been consumed, so the caller may reuse its
+ * buffer.  Errors: as ht_inc_update. */
+int ht_inc_update_host(ht_inc *h, const void *data_host, uint64_t len, ht_stream_t stream);
+
+/* Writes the k digest words of the string to digest_dev (device) and closes
+ * it (ht_inc_init opens the next one).  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_inc_final(ht_inc *h, uint64_t *digest_dev, ht_stream_t stream);
+
+/* Bytes appended so far to the open string. */
+uint64_t ht_inc_length(const ht_inc *h);
+
+/* Bytes of one chunk (64 executions): updates whose lengths are multiples of
+ * this, from a string start, copy nothing. */
+uint64_t ht_inc_granule(const ht_inc *h);
+
+/* Size in bytes of a saved state (header, stack, chunk buffer). */
+size_t ht_inc_state_bytes(const ht_inc *h);
+
+/* Saves the open string's state into state_host (n >= ht_inc_state_bytes
+ * bytes, host memory); waits for `stream`.  The state records the width and
+ * a fingerprint of the seed words.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_inc_export(const ht_inc *h, void *state_host, size_t n, ht_stream_t stream);
+
+/* Replaces the handle's string by a saved state; waits for `stream`.
+ * Errors: HT_ERR_ARG (short buffer, other width or seed words, corrupt
+ * header), HT_ERR_CUDA. */
+int ht_inc_import(ht_inc *h, const void *state_host, size_t n, ht_stream_t stream);
 
 /* ---- hashing without allocation ---------------------------------------------
  * (The paper has no counterpart: this serves deployments, not the method.)

@@ -10,7 +10,7 @@ import importlib
 
 import numpy as np
 
-__all__ = ["abi", "HalftimeError", "WIDTHS", "Hasher", "digest_words"]
+__all__ = ["abi", "HalftimeError", "WIDTHS", "Hasher", "Incremental", "digest_words"]
 WIDTHS = (16, 24, 32, 40)
 
 
@@ -102,3 +102,73 @@ class Hasher:
 
     def launches(self) -> int:
         return _abi().ht_ctx_launches(self.ctx)
+
+    def incremental(self) -> "Incremental":
+        """A handle for one string given in pieces (init / update / final)."""
+        return Incremental(self)
+
+
+class Incremental:
+    """Incremental hashing over a Hasher's context: update() with pieces in
+    order (CUDA uint8 tensors or host numpy arrays), then final().  The
+    digest equals Hasher.hash of the concatenated pieces."""
+
+    def __init__(self, hasher: Hasher):
+        self.hasher = hasher
+        self.k = hasher.k
+        self.h = _abi().ht_inc_create(hasher.ctx)
+
+    def close(self):
+        if self.h:
+            _abi().ht_inc_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        return stream if stream is not None else torch.cuda.current_stream()
+
+    def init(self, stream=None):
+        _abi().ht_inc_init(self.h, self._stream(stream))
+
+    def update(self, data, stream=None):
+        """Appends a CUDA tensor's bytes (device) or a numpy array's (host)."""
+        if isinstance(data, np.ndarray):
+            data = np.ascontiguousarray(data).view(np.uint8).reshape(-1)
+            _abi().ht_inc_update_host(self.h, data.ctypes.data if data.size else None, data.size,
+                                      self._stream(stream))
+        else:
+            n = data.numel() * data.element_size()
+            _abi().ht_inc_update(self.h, data.data_ptr() if n else None, n, self._stream(stream))
+
+    def final(self, out=None, stream=None):
+        """Digest as a CUDA int64 tensor of k words (uint64 bit patterns)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.k, dtype=torch.int64, device="cuda")
+        _abi().ht_inc_final(self.h, out.data_ptr(), self._stream(stream))
+        return out
+
+    def length(self) -> int:
+        return _abi().ht_inc_length(self.h)
+
+    def granule(self) -> int:
+        return _abi().ht_inc_granule(self.h)
+
+    def export_state(self, stream=None) -> bytes:
+        return _abi().ht_inc_export(self.h, self._stream(stream))
+
+    def import_state(self, state: bytes, stream=None):
+        _abi().ht_inc_import(self.h, state, self._stream(stream))

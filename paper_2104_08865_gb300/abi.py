@@ -83,6 +83,17 @@ _PROTOS = {
     "ht_hash_batch": (_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "ht_hash_batch_naive": (_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "ht_hash_noalloc": (_int, [_int, _u64p, _sz, _vp, _u64, _vp, _vp]),
+    "ht_inc_create": (_int, [_vp, ctypes.POINTER(_vp)]),
+    "ht_inc_destroy": (_int, [_vp]),
+    "ht_inc_init": (_int, [_vp, _vp]),
+    "ht_inc_update": (_int, [_vp, _vp, _u64, _vp]),
+    "ht_inc_update_host": (_int, [_vp, _vp, _u64, _vp]),
+    "ht_inc_final": (_int, [_vp, _vp, _vp]),
+    "ht_inc_length": (_u64, [_vp]),
+    "ht_inc_granule": (_u64, [_vp]),
+    "ht_inc_state_bytes": (_sz, [_vp]),
+    "ht_inc_export": (_int, [_vp, _vp, _sz, _vp]),
+    "ht_inc_import": (_int, [_vp, _vp, _sz, _vp]),
     "ht_part_granule": (_u64, [_vp]),
     "ht_part_state_words": (_sz, [_vp, _u64]),
     "ht_part_begin": (_int, [_vp, _u64, _vp, _sz, _vp]),
@@ -234,6 +245,56 @@ def ht_hash_noalloc(width: int, seed_words, data_dev, length: int, digest_dev, s
     seed_words = np.ascontiguousarray(seed_words, dtype=np.uint64)
     _check(_lib.ht_hash_noalloc(width, seed_words.ctypes.data_as(_u64p), seed_words.size,
                                 _ptr(data_dev), length, _ptr(digest_dev), _stream(stream)))
+
+
+def ht_inc_create(ctx: int) -> int:
+    h = _vp()
+    _check(_lib.ht_inc_create(ctx, ctypes.byref(h)))
+    return h.value
+
+
+def ht_inc_destroy(h: int) -> None:
+    _check(_lib.ht_inc_destroy(h))
+
+
+def ht_inc_init(h: int, stream=None) -> None:
+    _check(_lib.ht_inc_init(h, _stream(stream)))
+
+
+def ht_inc_update(h: int, data_dev, length: int, stream=None) -> None:
+    _check(_lib.ht_inc_update(h, _ptr(data_dev), length, _stream(stream)))
+
+
+def ht_inc_update_host(h: int, data_host, length: int, stream=None) -> None:
+    _check(_lib.ht_inc_update_host(h, _ptr(data_host), length, _stream(stream)))
+
+
+def ht_inc_final(h: int, digest_dev, stream=None) -> None:
+    _check(_lib.ht_inc_final(h, _ptr(digest_dev), _stream(stream)))
+
+
+def ht_inc_length(h: int) -> int:
+    return int(_lib.ht_inc_length(h))
+
+
+def ht_inc_granule(h: int) -> int:
+    return int(_lib.ht_inc_granule(h))
+
+
+def ht_inc_state_bytes(h: int) -> int:
+    return int(_lib.ht_inc_state_bytes(h))
+
+
+def ht_inc_export(h: int, stream=None) -> bytes:
+    """The open string's saved state (host bytes)."""
+    buf = ctypes.create_string_buffer(ht_inc_state_bytes(h))
+    _check(_lib.ht_inc_export(h, buf, len(buf), _stream(stream)))
+    return buf.raw
+
+
+def ht_inc_import(h: int, state: bytes, stream=None) -> None:
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    _check(_lib.ht_inc_import(h, buf, len(state), _stream(stream)))
 
 
 def ht_part_granule(ctx: int) -> int:

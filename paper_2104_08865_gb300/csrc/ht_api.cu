@@ -161,7 +161,7 @@ static Scratch scratch_view(const ht_ctx *c) {
   return s;
 }
 
-static void fill_keys(const ht_ctx *c, KParams &P) {
+void fill_keys(const ht_ctx *c, KParams &P) {
   const KernelSet &ks = *c->ks;
   memset(&P, 0, sizeof P);
   for (int i = 0; i < ks.ew; ++i) P.E[i] = c->h_seeds[i];

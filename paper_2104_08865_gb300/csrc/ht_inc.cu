@@ -1,0 +1,408 @@
+// ht_inc.cu -- incremental hashing: a string given in pieces of any length,
+// one after another, whose total length is known only at the end.
+//
+// The handle holds the string's eager tree counter between calls (Section
+// 5.2: the pending nodes of every level, kept on a stack) and a buffer for
+// bytes that do not yet fill a 64-execution chunk.  Updates run the
+// warp-chunk kernel in its incremental mode over whole chunks, straight from
+// the caller's memory; only the bytes that straddle an update boundary are
+// copied.  The final call hashes the stack's pending nodes, the buffered
+// executions and the tail.  The digest equals the one-shot digest of the
+// concatenated pieces.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "halftime.h"
+#include "ht_internal.h"
+#include "ht_runtime.h"
+#include "ht_spec.cuh"
+
+using namespace ht;
+
+namespace {
+
+constexpr int kChunkExecs = 64;             // executions per chunk (a level-2 node)
+constexpr uint64_t kMaxChunks = 1u << 16;   // chunks per update launch
+constexpr uint64_t kStageChunks = 1024;     // chunks per staging slot of host updates
+constexpr int kStageSlots2 = 2;
+constexpr uint64_t kStateMagic = 0x31636e4948544831ull;  // "1HTHInc1"
+constexpr int kTpb = 256;
+
+// Group slots an update of chunks [C, C + M) can complete: at level l >= 2,
+// the groups between the ones holding node C >> 3(l-2) and node
+// (C + M) >> 3(l-2).
+uint64_t groups_for_update(uint64_t C, uint64_t M) {
+  uint64_t g = 0;
+  const uint64_t N0 = C * kChunkExecs, N1 = (C + M) * kChunkExecs;
+  for (int lvl = 2; lvl < kLevels - 1; ++lvl) g += ((N1 >> (3 * lvl)) >> 3) - ((N0 >> (3 * lvl)) >> 3);
+  return g;
+}
+
+// Whether some level's incomplete group holds stack nodes (d > 0) and is
+// completed by the update, so its accumulator must be seeded first.
+bool needs_seed(uint64_t C, uint64_t M) {
+  const uint64_t N0 = C * kChunkExecs, N1 = (C + M) * kChunkExecs;
+  for (int lvl = 2; lvl < kLevels - 1; ++lvl) {
+    const uint64_t n0 = N0 >> (3 * lvl), n1 = N1 >> (3 * lvl);
+    if ((n0 & 7) && (n1 >> 3) > (n0 >> 3)) return true;
+  }
+  return false;
+}
+
+uint64_t seed_fingerprint(const ht_ctx *c) {
+  uint64_t h = 0xcbf29ce484222325ull;  // FNV-1a over the seed words' bytes
+  for (uint64_t w : c->h_seeds)
+    for (int i = 0; i < 8; ++i) {
+      h ^= (w >> (8 * i)) & 0xff;
+      h *= 0x100000001b3ull;
+    }
+  return h;
+}
+
+}  // namespace
+
+struct ht_inc {
+  ht_ctx *ctx = nullptr;
+  int k = 0;
+  uint64_t granule = 0;  // bytes of one chunk
+  uint64_t cap_groups = 0;
+  // device state
+  unsigned long long *grp_acc = nullptr;
+  unsigned int *grp_cnt = nullptr;
+  unsigned long long *str_acc = nullptr;
+  unsigned int *str_done = nullptr;
+  Ctl *ctl = nullptr;
+  unsigned long long *stack = nullptr;
+  uint8_t *buf = nullptr;
+  // host mirror of the counter
+  uint64_t chunks = 0;  // whole chunks hashed
+  uint64_t fill = 0;    // bytes waiting in buf (< granule)
+  bool open = false;
+  // host updates: staging slots filled on a copy stream
+  cudaStream_t copy_stream = nullptr;
+  uint8_t *stage[kStageSlots2] = {nullptr, nullptr};
+  cudaEvent_t ev_copy[kStageSlots2] = {nullptr, nullptr};
+  cudaEvent_t ev_hash[kStageSlots2] = {nullptr, nullptr};
+  uint64_t piece = 0;
+};
+
+namespace {
+
+size_t stack_words(const ht_inc *h) { return (size_t)kLevels * kFan * h->k * kLanes; }
+
+void inc_params(const ht_inc *h, KParams &P) {
+  fill_keys(h->ctx, P);
+  P.scr.grp_acc = h->grp_acc;
+  P.scr.grp_cnt = h->grp_cnt;
+  P.scr.str_acc = h->str_acc;
+  P.scr.str_done = h->str_done;
+  P.scr.ctl = h->ctl;
+  P.scr.cap_groups = h->cap_groups;
+  P.stack = h->stack;
+  P.count = 1;
+}
+
+// Hashes chunks [h->chunks, h->chunks + M) found at ptr (device).
+int run_chunks(ht_inc *h, const uint8_t *ptr, uint64_t M, cudaStream_t s) {
+  ht_ctx *c = h->ctx;
+  const KernelSet &ks = *c->ks;
+  const uint64_t C = h->chunks;
+  if (groups_for_update(C, M) > h->cap_groups)
+    return set_error(HT_ERR_ARG, "incremental update needs more group slots than reserved");
+  KParams P;
+  inc_params(h, P);
+  StrPlan &sp = P.single;
+  sp.ptr = ptr - C * h->granule;  // the kernel addresses the string from its start
+  sp.n_exec = (C + M) * kChunkExecs;
+  sp.len = sp.n_exec * (uint64_t)ks.exec_bytes;
+  sp.chunk0 = C;
+  sp.n_items = 0xffffffffu;
+  void *args[] = {&P};
+  cudaError_t e;
+  if (needs_seed(C, M)) {
+    e = cudaLaunchKernel(ks.inc_seed, dim3(1), dim3(32), args, 0, s);
+    if (e != cudaSuccess) return cuda_error(e, "incremental seed launch");
+    c->launches.fetch_add(1);
+  }
+  const void *func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.inc_aligned : ks.inc_unaligned;
+  int bps = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, func, kTpb, 0);
+  if (e != cudaSuccess) return cuda_error(e, "occupancy");
+  bps = std::max(1, std::min(bps, 2));
+  const uint64_t wpb = kTpb / 32;
+  // whole rounds of cursor grabs (see the one-shot launch)
+  const uint64_t wmax = (uint64_t)c->num_sms * bps * wpb;
+  const uint64_t rounds = (M + wmax - 1) / wmax;
+  const uint64_t warps = (M + rounds - 1) / rounds;
+  const uint64_t grid = std::max<uint64_t>(1, (warps + wpb - 1) / wpb);
+  P.item_begin = C;
+  P.item_end = C + M;
+  P.total_warps = (unsigned)(grid * wpb);
+  e = cudaLaunchKernel(func, dim3((unsigned)grid), dim3(kTpb), args, 0, s);
+  if (e != cudaSuccess) return cuda_error(e, "incremental update launch");
+  c->launches.fetch_add(1);
+  h->chunks = C + M;
+  return HT_OK;
+}
+
+void free_inc(ht_inc *h) {
+  cudaFree(h->grp_acc);
+  cudaFree(h->grp_cnt);
+  cudaFree(h->str_acc);
+  cudaFree(h->str_done);
+  cudaFree(h->ctl);
+  cudaFree(h->stack);
+  cudaFree(h->buf);
+  for (int i = 0; i < kStageSlots2; ++i) {
+    cudaFree(h->stage[i]);
+    if (h->ev_copy[i]) cudaEventDestroy(h->ev_copy[i]);
+    if (h->ev_hash[i]) cudaEventDestroy(h->ev_hash[i]);
+  }
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+}
+
+#define INC_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_error(e_, #call); \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int ht_inc_create(ht_ctx *c, ht_inc **out) {
+  if (!c || !out) return set_error(HT_ERR_ARG, "ht_inc_create: NULL argument");
+  *out = nullptr;
+  ht_inc *h = new ht_inc;
+  h->ctx = c;
+  h->k = c->ks->k;
+  h->granule = (uint64_t)kChunkExecs * (uint64_t)c->ks->exec_bytes;
+  h->cap_groups = kMaxChunks / 7 + 2 * kLevels;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void **p, size_t n) {
+    if (e == cudaSuccess) e = cudaMalloc(p, n);
+  };
+  alloc((void **)&h->grp_acc, h->cap_groups * h->k * kLanes * sizeof(unsigned long long));
+  alloc((void **)&h->grp_cnt, h->cap_groups * sizeof(unsigned int));
+  alloc((void **)&h->str_acc, 8 * sizeof(unsigned long long));
+  alloc((void **)&h->str_done, 256);
+  alloc((void **)&h->ctl, sizeof(Ctl));
+  alloc((void **)&h->stack, stack_words(h) * sizeof(unsigned long long));
+  alloc((void **)&h->buf, h->granule);
+  if (e != cudaSuccess) {
+    free_inc(h);
+    delete h;
+    return cuda_error(e, "ht_inc_create allocation");
+  }
+  const int rc = ht_inc_init(h, nullptr);
+  if (rc != HT_OK) {
+    free_inc(h);
+    delete h;
+    return rc;
+  }
+  e = cudaStreamSynchronize(nullptr);
+  if (e != cudaSuccess) {
+    free_inc(h);
+    delete h;
+    return cuda_error(e, "ht_inc_create");
+  }
+  *out = h;
+  return HT_OK;
+}
+
+int ht_inc_destroy(ht_inc *h) {
+  if (!h) return HT_OK;
+  cudaDeviceSynchronize();
+  free_inc(h);
+  delete h;
+  return HT_OK;
+}
+
+int ht_inc_init(ht_inc *h, ht_stream_t stream) {
+  if (!h) return set_error(HT_ERR_ARG, "ht_inc_init: NULL handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  INC_CUDA(cudaMemsetAsync(h->grp_acc, 0, h->cap_groups * h->k * kLanes * sizeof(unsigned long long), s));
+  INC_CUDA(cudaMemsetAsync(h->grp_cnt, 0, h->cap_groups * sizeof(unsigned int), s));
+  INC_CUDA(cudaMemsetAsync(h->str_acc, 0, 8 * sizeof(unsigned long long), s));
+  INC_CUDA(cudaMemsetAsync(h->str_done, 0, 256, s));
+  INC_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
+  h->chunks = 0;
+  h->fill = 0;
+  h->open = true;
+  return HT_OK;
+}
+
+uint64_t ht_inc_length(const ht_inc *h) { return h ? h->chunks * h->granule + h->fill : 0; }
+
+uint64_t ht_inc_granule(const ht_inc *h) { return h ? h->granule : 0; }
+
+int ht_inc_update(ht_inc *h, const void *data_dev, uint64_t len, ht_stream_t stream) {
+  if (!h || !h->open) return set_error(HT_ERR_ARG, "ht_inc_update: call ht_inc_init first");
+  if (len && !data_dev) return set_error(HT_ERR_ARG, "ht_inc_update: NULL data");
+  if (len > ~0ull - ht_inc_length(h)) return set_error(HT_ERR_TOO_LONG, "ht_inc_update: string longer than 2^64 - 1 bytes");
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint8_t *p = static_cast<const uint8_t *>(data_dev);
+  uint64_t m = len;
+  if (h->fill) {
+    // complete the buffered chunk first
+    const uint64_t r = std::min(m, h->granule - h->fill);
+    if (r) INC_CUDA(cudaMemcpyAsync(h->buf + h->fill, p, r, cudaMemcpyDeviceToDevice, s));
+    h->fill += r;
+    p += r;
+    m -= r;
+    if (h->fill < h->granule) return HT_OK;
+    const int rc = run_chunks(h, h->buf, 1, s);
+    if (rc) return rc;
+    h->fill = 0;
+  }
+  uint64_t M = m / h->granule;
+  while (M) {
+    const uint64_t piece = std::min(M, kMaxChunks);
+    const int rc = run_chunks(h, p, piece, s);
+    if (rc) return rc;
+    p += piece * h->granule;
+    m -= piece * h->granule;
+    M -= piece;
+  }
+  if (m) {
+    INC_CUDA(cudaMemcpyAsync(h->buf, p, m, cudaMemcpyDeviceToDevice, s));
+    h->fill = m;
+  }
+  return HT_OK;
+}
+
+int ht_inc_update_host(ht_inc *h, const void *data_host, uint64_t len, ht_stream_t stream) {
+  if (!h || !h->open) return set_error(HT_ERR_ARG, "ht_inc_update_host: call ht_inc_init first");
+  if (len && !data_host) return set_error(HT_ERR_ARG, "ht_inc_update_host: NULL data");
+  if (len > ~0ull - ht_inc_length(h))
+    return set_error(HT_ERR_TOO_LONG, "ht_inc_update_host: string longer than 2^64 - 1 bytes");
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint8_t *p = static_cast<const uint8_t *>(data_host);
+  uint64_t m = len;
+  if (h->fill) {
+    const uint64_t r = std::min(m, h->granule - h->fill);
+    if (r) INC_CUDA(cudaMemcpyAsync(h->buf + h->fill, p, r, cudaMemcpyHostToDevice, s));
+    h->fill += r;
+    p += r;
+    m -= r;
+    if (h->fill < h->granule) return HT_OK;
+    const int rc = run_chunks(h, h->buf, 1, s);
+    if (rc) return rc;
+    h->fill = 0;
+  }
+  uint64_t M = m / h->granule;
+  if (M) {
+    const uint64_t slot_bytes = kStageChunks * h->granule;
+    if (!h->copy_stream) INC_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < kStageSlots2; ++i) {
+      if (!h->stage[i]) INC_CUDA(cudaMalloc((void **)&h->stage[i], slot_bytes));
+      if (!h->ev_copy[i]) INC_CUDA(cudaEventCreateWithFlags(&h->ev_copy[i], cudaEventDisableTiming));
+      if (!h->ev_hash[i]) INC_CUDA(cudaEventCreateWithFlags(&h->ev_hash[i], cudaEventDisableTiming));
+    }
+    // pieces alternate between two slots: the copy of one overlaps the
+    // hashing of the other
+    while (M) {
+      const uint64_t piece = std::min(M, kStageChunks);
+      const int slot = (int)(h->piece++ % kStageSlots2);
+      INC_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_hash[slot], 0));
+      INC_CUDA(cudaMemcpyAsync(h->stage[slot], p, piece * h->granule, cudaMemcpyHostToDevice, h->copy_stream));
+      INC_CUDA(cudaEventRecord(h->ev_copy[slot], h->copy_stream));
+      INC_CUDA(cudaStreamWaitEvent(s, h->ev_copy[slot], 0));
+      const int rc = run_chunks(h, h->stage[slot], piece, s);
+      if (rc) return rc;
+      INC_CUDA(cudaEventRecord(h->ev_hash[slot], s));
+      p += piece * h->granule;
+      m -= piece * h->granule;
+      M -= piece;
+    }
+  }
+  if (m) {
+    INC_CUDA(cudaMemcpyAsync(h->buf, p, m, cudaMemcpyHostToDevice, s));
+    h->fill = m;
+  }
+  // the caller may reuse its buffer once this returns (copies from pinned
+  // memory are asynchronous)
+  INC_CUDA(cudaStreamSynchronize(s));
+  return HT_OK;
+}
+
+int ht_inc_final(ht_inc *h, uint64_t *digest_dev, ht_stream_t stream) {
+  if (!h || !h->open) return set_error(HT_ERR_ARG, "ht_inc_final: call ht_inc_init first");
+  if (!digest_dev) return set_error(HT_ERR_ARG, "ht_inc_final: NULL digest");
+  ht_ctx *c = h->ctx;
+  const KernelSet &ks = *c->ks;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t C = h->chunks;
+  KParams P;
+  inc_params(h, P);
+  StrPlan &sp = P.single;
+  sp.ptr = h->buf - C * h->granule;
+  sp.len = C * h->granule + h->fill;
+  sp.n_exec = C * kChunkExecs + h->fill / (uint64_t)ks.exec_bytes;
+  sp.chunk0 = C;
+  sp.n_items = 1;  // the remainder launch below finishes the string
+  P.digests = reinterpret_cast<unsigned long long *>(digest_dev);
+  void *args[] = {&P};
+  if (C) {
+    INC_CUDA(cudaLaunchKernel(ks.inc_stack, dim3(1), dim3(32), args, 0, s));
+    c->launches.fetch_add(1);
+  }
+  // the buffered executions (fewer than one chunk: pending nodes of levels 0
+  // and 1) and the tail, by the one-shot kernel's last chunk of the string
+  P.item_begin = C;
+  P.item_end = C + 1;
+  P.total_warps = 1;
+  INC_CUDA(cudaLaunchKernel(ks.single_aligned[1], dim3(1), dim3(32), args, 0, s));
+  c->launches.fetch_add(1);
+  h->open = false;
+  return HT_OK;
+}
+
+size_t ht_inc_state_bytes(const ht_inc *h) {
+  return h ? 4 * sizeof(uint64_t) + stack_words(h) * sizeof(uint64_t) + h->granule : 0;
+}
+
+int ht_inc_export(const ht_inc *h, void *state_host, size_t n, ht_stream_t stream) {
+  if (!h || !h->open || !state_host) return set_error(HT_ERR_ARG, "ht_inc_export: no open string");
+  if (n < ht_inc_state_bytes(h)) return set_error(HT_ERR_ARG, "ht_inc_export: buffer of %zu bytes, need %zu", n, ht_inc_state_bytes(h));
+  cudaStream_t s = (cudaStream_t)stream;
+  uint64_t *hd = static_cast<uint64_t *>(state_host);
+  hd[0] = kStateMagic ^ (uint64_t)h->ctx->width;
+  hd[1] = seed_fingerprint(h->ctx);
+  hd[2] = h->chunks;
+  hd[3] = h->fill;
+  uint8_t *b = static_cast<uint8_t *>(state_host) + 4 * sizeof(uint64_t);
+  INC_CUDA(cudaMemcpyAsync(b, h->stack, stack_words(h) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  if (h->fill)
+    INC_CUDA(cudaMemcpyAsync(b + stack_words(h) * sizeof(uint64_t), h->buf, h->fill, cudaMemcpyDeviceToHost, s));
+  INC_CUDA(cudaStreamSynchronize(s));
+  return HT_OK;
+}
+
+int ht_inc_import(ht_inc *h, const void *state_host, size_t n, ht_stream_t stream) {
+  if (!h || !state_host) return set_error(HT_ERR_ARG, "ht_inc_import: NULL argument");
+  if (n < ht_inc_state_bytes(h)) return set_error(HT_ERR_ARG, "ht_inc_import: state of %zu bytes, need %zu", n, ht_inc_state_bytes(h));
+  const uint64_t *hd = static_cast<const uint64_t *>(state_host);
+  if (hd[0] != (kStateMagic ^ (uint64_t)h->ctx->width))
+    return set_error(HT_ERR_ARG, "ht_inc_import: not a state of a width-%d string", h->ctx->width);
+  if (hd[1] != seed_fingerprint(h->ctx))
+    return set_error(HT_ERR_ARG, "ht_inc_import: the state was made with other seed words");
+  if (hd[3] >= h->granule || hd[2] > (~0ull - hd[3]) / h->granule)
+    return set_error(HT_ERR_ARG, "ht_inc_import: corrupt state");
+  int rc = ht_inc_init(h, stream);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint8_t *b = static_cast<const uint8_t *>(state_host) + 4 * sizeof(uint64_t);
+  INC_CUDA(cudaMemcpyAsync(h->stack, b, stack_words(h) * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  if (hd[3])
+    INC_CUDA(cudaMemcpyAsync(h->buf, b + stack_words(h) * sizeof(uint64_t), hd[3], cudaMemcpyHostToDevice, s));
+  INC_CUDA(cudaStreamSynchronize(s));
+  h->chunks = hd[2];
+  h->fill = hd[3];
+  return HT_OK;
+}
+
+}  // extern "C"

@@ -8,7 +8,10 @@
 
 namespace ht {
 
-// One string of a launch, as the planner lays it out.
+// One string of a launch, as the planner lays it out.  In incremental mode
+// (one update of whole 64-execution chunks) chunk0 is the number of chunks
+// the string held before the update and n_exec counts the executions up to
+// the update's end.
 struct StrPlan {
   const uint8_t *ptr;  // first byte of the string (device)
   uint64_t len;        // bytes
@@ -63,6 +66,7 @@ struct KParams {
   const unsigned long long *chunk0s;  // batch mode: chunk0 of each string (+ total)
   const unsigned long long *unitb0s;  // batch mode: unitb0 of each string (+ total)
   unsigned long long *digests;  // count * k words
+  unsigned long long *stack;    // incremental mode: pending nodes [level][8][k][8]
   StrPlan single;               // single-string mode: the string
   unsigned long long item_begin, item_end;  // single mode: item range of this launch
   unsigned int count;           // batch mode: strings
@@ -101,6 +105,10 @@ struct KernelSet {
   const void *range_batch_unaligned;
   const void *part_tail;    // parts: tail NH of the last part
   const void *part_finish;  // parts: climb merged groups, write the digest
+  const void *inc_aligned;    // incremental: whole chunks of one update
+  const void *inc_unaligned;
+  const void *inc_seed;       // incremental: frontier groups from the stack
+  const void *inc_stack;      // incremental: pending stack nodes into the sum
   int exec_bytes, k, n_seed, off_T, off_F, off_R, ew;
 };
 

@@ -262,9 +262,15 @@ __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx
 
 // ---- one work item: a chunk of 8^L executions ---------------------------------
 
-template <int W, int L, bool ALIGNED>
+// INC: one update of incremental hashing (L = 2, whole chunks only).  Chunk
+// indices are global in the string; groups are slotted from the first group
+// of each level that the update touches, and nodes still pending at the end
+// of the update are stored one by one on the stack instead of being hashed
+// with their final keys (their positions change as the string grows).
+template <int W, int L, bool ALIGNED, bool INC = false>
 __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
                            uint64_t c, int ln) {
+  static_assert(!INC || L == 2, "incremental updates run 64-execution chunks");
   constexpr int k = Spec<W>::k;
   constexpr uint64_t B = Dims<W>::exec_bytes;
   constexpr uint64_t CH = 1ull << (3 * L);
@@ -408,17 +414,28 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
         const uint64_t first_pending = C & ~7ull;
         if (idx >= first_pending) {
           const uint64_t j = idx - first_pending;
+          if constexpr (INC) {
+            if (x < k) {
+              unsigned long long *st = P.stack + (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
+              st[0] = v0;
+              st[1] = v1;
+            }
+          } else {
 #pragma unroll
-          for (int t = 0; t < k; ++t)
-            if (x == t)
-              pend[t] += nh64(v0, final_key<W>(P, t, lvl, j, 2 * p)) +
-                         nh64(v1, final_key<W>(P, t, lvl, j, 2 * p + 1));
-          anyp = true;
+            for (int t = 0; t < k; ++t)
+              if (x == t)
+                pend[t] += nh64(v0, final_key<W>(P, t, lvl, j, 2 * p)) +
+                           nh64(v1, final_key<W>(P, t, lvl, j, 2 * p + 1));
+            anyp = true;
+          }
           break;
         }
         const uint64_t g = idx >> 3;
         const int pos = (int)(idx & 7);
-        const uint64_t slot = sp.grp0 + goff + g;
+        // first group of this level in the scratch (incremental: the group
+        // the update starts in)
+        const uint64_t gbase = INC ? (((sp.chunk0 << 6) >> (3 * lvl)) >> 3) : 0;
+        const uint64_t slot = sp.grp0 + goff + (g - gbase);
         unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
         if (x < k) {
           uint64_t a0 = v0, a1 = v1;
@@ -445,12 +462,13 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
           acc[1] = 0;
         }
         if (ln == 0) P.scr.grp_cnt[slot] = 0;
-        goff += C >> 3;
+        goff += (C >> 3) - gbase;
         lvl += 1;
         idx = g;
       }
     }
   }
+  if constexpr (INC) return;  // nothing is final before the string ends
 
   griddep_wait();
   if (__any_sync(kFull, anyp)) {
@@ -496,8 +514,9 @@ __device__ __forceinline__ void exit_protocol(const KParams &P, int ln) {
   }
 }
 
-template <int W, int L, bool SINGLE, bool ALIGNED>
+template <int W, int L, bool SINGLE, bool ALIGNED, bool INC = false>
 __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KParams P) {
+  static_assert(!INC || SINGLE, "incremental updates hash one string");
   const int ln = threadIdx.x & 31;
   uint64_t total;
   if (SINGLE) {
@@ -529,7 +548,7 @@ __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KP
     }
     if (item >= total) break;
     if (SINGLE) {
-      hash_chunk<W, L, ALIGNED>(P, P.single, 0, item, ln);
+      hash_chunk<W, L, ALIGNED, INC>(P, P.single, 0, item, ln);
     } else {
       const unsigned s = find_string(P.item0s, P.count, item);
       const StrPlan sp = P.plans[s];

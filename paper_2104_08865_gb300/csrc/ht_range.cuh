@@ -14,6 +14,7 @@
 // as in the stream kernel.
 #pragma once
 
+#include "ht_inc.cuh"
 #include "ht_parts.cuh"
 #include "ht_stream.cuh"
 
@@ -262,6 +263,10 @@ KernelSet make_kernel_set() {
   ks.range_batch_unaligned = (const void *)range_kernel<W, true, false>;
   ks.part_tail = (const void *)part_tail_kernel<W>;
   ks.part_finish = (const void *)part_finish_kernel<W, 2>;
+  ks.inc_aligned = (const void *)hash_kernel<W, 2, true, true, true>;
+  ks.inc_unaligned = (const void *)hash_kernel<W, 2, true, false, true>;
+  ks.inc_seed = (const void *)inc_seed_kernel<W>;
+  ks.inc_stack = (const void *)inc_stack_kernel<W>;
   ks.exec_bytes = Dims<W>::exec_bytes;
   ks.k = Spec<W>::k;
   ks.n_seed = Dims<W>::n_seed;

@@ -63,4 +63,6 @@ int cuda_error(cudaError_t e, const char *what);
 const KernelSet *kernel_set(int width);
 uint64_t items_of(uint64_t N, int L);
 uint64_t groups_of(uint64_t N, int L);
+// Zeroes P, then fills the hash keys, the seed pointer and the context's scratch.
+void fill_keys(const ht_ctx *c, KParams &P);
 }  // namespace ht
