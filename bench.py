@@ -286,6 +286,69 @@ def run_batch(args, dev, stream):
             "digests_equal": same}
 
 
+def run_incremental(args, dev, stream, data, want):
+    """The benchmark's string hashed incrementally at width 24 (init / update /
+    final): device-resident pieces of 64 MiB and of 1 MiB + 3 bytes (every
+    piece boundary inside a chunk, so each update also copies a partial
+    chunk), and pinned host pieces of 64 MiB through the host update.  The
+    digest must equal the one-shot digest."""
+    import numpy as np
+    import torch
+
+    from paper_2104_08865_gb300 import Hasher, abi
+    w = 24
+    n = data.numel()
+    h = Hasher(w, seed_words=abi.ht_seed_expand(SEED_KEY, w))
+    inc = h.incremental()
+    out = torch.empty(w // 8, dtype=torch.int64, device=dev)
+    res = {"workload": "one %d MiB string, width 24, fed in pieces" % (n >> 20)}
+
+    def run_dev(piece):
+        inc.init(stream)
+        for o in range(0, n, piece):
+            inc.update(data[o:o + piece], stream)
+        inc.final(out, stream)
+
+    same = True
+    for name, piece, reps in (("device_64mib", 64 << 20, 10), ("device_1mib_plus_3", (1 << 20) + 3, 3)):
+        run_dev(piece)
+        torch.cuda.synchronize()
+        same &= out.cpu().numpy().view(np.uint64).tolist() == want
+        l0 = h.launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run_dev(piece)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"gbs": round(n / ms / 1e6, 1), "ms": round(ms, 3),
+                     "launches": (h.launches() - l0) // reps}
+    pinned = torch.empty(n, dtype=torch.uint8).pin_memory()
+    pinned.copy_(data)
+    hp = pinned.numpy()
+    piece = 64 << 20
+
+    def run_host():
+        inc.init(stream)
+        for o in range(0, n, piece):
+            inc.update(hp[o:o + piece], stream)
+        inc.final(out, stream)
+        torch.cuda.synchronize()
+
+    run_host()
+    same &= out.cpu().numpy().view(np.uint64).tolist() == want
+    t0 = time.perf_counter()
+    for _ in range(3):
+        run_host()
+    dt = (time.perf_counter() - t0) / 3
+    res["host_pinned_64mib"] = {"gbs": round(n / dt / 1e9, 1), "ms": round(dt * 1e3, 3)}
+    res["digest_equals_one_shot"] = bool(same)
+    inc.close()
+    h.close()
+    return res
+
+
 def run_serving(args, dev, stream):
     """C5: Poisson arrivals of width-32 hash requests, lengths log-uniform in
     [256 B, 64 MiB], 16 GiB admission budget; offered load swept over
@@ -481,6 +544,8 @@ def run_gpu(args):
                "digests_match_gpu": match}
 
     batch = run_batch(args, dev, stream) if not args.no_batch else None
+    incremental = (run_incremental(args, dev, stream, data, digests[24])
+                   if (rank == 0 and not args.no_inc) else None)
     serving = run_serving(args, dev, stream) if (rank == 0 and not args.no_serve) else None
 
     if rank == 0:
@@ -505,7 +570,7 @@ def run_gpu(args):
                          "peak_source": peak_kind},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": ck,
             "shapes": shapes,
-            "batch": batch, "serving": serving,
+            "batch": batch, "incremental": incremental, "serving": serving,
             "digests": {str(w): ["%016x" % v for v in digests[w]] for w in WIDTHS},
         }
         print(json.dumps(line), flush=True)
@@ -534,6 +599,7 @@ def main():
     ap.add_argument("--no-overlap", action="store_true",
                     help="time the step without overlapping consecutive launches")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-inc", action="store_true", help="skip the incremental-hashing leg")
     ap.add_argument("--batch-strings", type=int, default=50_000)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
