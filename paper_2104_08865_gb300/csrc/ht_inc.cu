@@ -343,7 +343,7 @@ int ht_inc_final(ht_inc *h, uint64_t *digest_dev, ht_stream_t stream) {
   sp.len = C * h->granule + h->fill;
   sp.n_exec = C * kChunkExecs + h->fill / (uint64_t)ks.exec_bytes;
   sp.chunk0 = C;
-  sp.n_items = 1;  // the remainder launch below finishes the string
+  sp.n_items = 1;  // reached by the remainder launch below (items [C, C + 1)): it ends the string
   P.digests = reinterpret_cast<unsigned long long *>(digest_dev);
   void *args[] = {&P};
   if (C) {

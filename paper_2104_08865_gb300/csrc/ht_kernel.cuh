@@ -262,30 +262,29 @@ __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx
 
 // ---- one work item: a chunk of 8^L executions ---------------------------------
 
-// INC: one update of incremental hashing (L = 2, whole chunks only).  Chunk
-// indices are global in the string; groups are slotted from the first group
-// of each level that the update touches, and nodes still pending at the end
-// of the update are stored one by one on the stack instead of being hashed
-// with their final keys (their positions change as the string grows).
-template <int W, int L, bool ALIGNED, bool INC = false>
-__device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
-                           uint64_t c, int ln) {
-  static_assert(!INC || L == 2, "incremental updates run 64-execution chunks");
+constexpr uint64_t kNoNode = ~0ull;
+
+// Levels 0..L of chunk c of a string (Section 5.2 tree, Eq. stack-construction):
+// the EHC values of its executions, level 1 in registers, level 2 across the
+// eight x-threads, level 3 over eight sub-chunks (L = 3).  A full chunk's root
+// (node c of level L) is returned in (v0, v1) of thread x < k (tree x, lanes
+// 2p and 2p+1); the leaves and nodes of the string's last, incomplete chunk
+// are pending roots, whose final NH goes into pend.  Returns whether the
+// chunk is full.  Touches no scratch.
+template <int W, int L, bool ALIGNED>
+__device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, uint64_t c, int ln,
+                                           uint64_t (&pend)[Spec<W>::k], bool &anyp,
+                                           uint64_t &v0, uint64_t &v1) {
   constexpr int k = Spec<W>::k;
   constexpr uint64_t B = Dims<W>::exec_bytes;
   constexpr uint64_t CH = 1ull << (3 * L);
   const int x = ln >> 2, p = ln & 3;
   const uint64_t N = sp.n_exec;
   const uint32_t sh = ALIGNED ? 0u : (uint32_t)(((uintptr_t)sp.ptr) & 15u);
-
-  uint64_t pend[k];  // this thread's share of the final-NH sum
-#pragma unroll
-  for (int t = 0; t < k; ++t) pend[t] = 0;
-  bool anyp = false;
-
+  const bool full = c * CH < N && (N - c * CH) >= CH;
   const uint64_t e0 = c * CH;
-  if (e0 < N) {
-    const bool full = (N - e0) >= CH;
+  if (e0 >= N) return false;
+  {
     uint64_t root[2][k];
 #pragma unroll
     for (int l = 0; l < 2; ++l)
@@ -395,82 +394,129 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
       }
     }
 
-    // everything below touches the context's scratch: an overlapping launch
-    // must first see its predecessor finish
-    griddep_wait();
-    if (full) {
-      // climb from the chunk root (level L, index c); thread x owns tree x
-      uint64_t v0 = 0, v1 = 0;
+    v0 = 0;
+    v1 = 0;
+#pragma unroll
+    for (int t = 0; t < k; ++t)
+      if (x == t) {
+        v0 = root[0][t];
+        v1 = root[1][t];
+      }
+  }
+  return full;
+}
+
+// First group of level-lvl nodes that the launch's scratch holds (an
+// incremental update counts from the group it starts in).
+template <bool INC>
+__device__ __forceinline__ uint64_t group_base(const StrPlan &sp, int lvl) {
+  return INC ? (((sp.chunk0 << 6) >> (3 * lvl)) >> 3) : 0;
+}
+
+// Slot offset of level lvl + 1's groups, given level lvl's.
+template <bool INC>
+__device__ __forceinline__ uint64_t next_goff(const StrPlan &sp, int lvl, uint64_t goff) {
+  return goff + ((sp.n_exec >> (3 * lvl)) >> 3) - group_base<INC>(sp, lvl);
+}
+
+// Node idx of level lvl, value (v0, v1) in thread x < k.  In the last,
+// incomplete group of its level it is a pending root: its final NH goes into
+// pend (or, in an incremental update, the node itself onto the stack, since
+// its final position is not known yet).  Otherwise its contribution to its
+// parent, NH under the tree key of its position (the eighth child enters
+// unhashed), is added into the group's accumulator.
+// Returns the group's slot, or kNoNode for a pending root.
+template <int W, bool INC>
+__device__ __forceinline__ uint64_t add_node(const KParams &P, const StrPlan &sp, int lvl, uint64_t idx,
+                                             uint64_t goff, uint64_t v0, uint64_t v1, int ln,
+                                             uint64_t (&pend)[Spec<W>::k], bool &anyp) {
+  constexpr int k = Spec<W>::k;
+  const int x = ln >> 2, p = ln & 3;
+  const uint64_t C = sp.n_exec >> (3 * lvl);
+  const uint64_t first_pending = C & ~7ull;
+  if (idx >= first_pending) {
+    const uint64_t j = idx - first_pending;
+    if constexpr (INC) {
+      if (x < k) {
+        unsigned long long *st = P.stack + (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
+        st[0] = v0;
+        st[1] = v1;
+      }
+    } else {
 #pragma unroll
       for (int t = 0; t < k; ++t)
-        if (x == t) {
-          v0 = root[0][t];
-          v1 = root[1][t];
-        }
-      int lvl = L;
-      uint64_t idx = c, goff = 0;
-      for (;;) {
-        const uint64_t C = N >> (3 * lvl);
-        const uint64_t first_pending = C & ~7ull;
-        if (idx >= first_pending) {
-          const uint64_t j = idx - first_pending;
-          if constexpr (INC) {
-            if (x < k) {
-              unsigned long long *st = P.stack + (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
-              st[0] = v0;
-              st[1] = v1;
-            }
-          } else {
-#pragma unroll
-            for (int t = 0; t < k; ++t)
-              if (x == t)
-                pend[t] += nh64(v0, final_key<W>(P, t, lvl, j, 2 * p)) +
-                           nh64(v1, final_key<W>(P, t, lvl, j, 2 * p + 1));
-            anyp = true;
-          }
-          break;
-        }
-        const uint64_t g = idx >> 3;
-        const int pos = (int)(idx & 7);
-        // first group of this level in the scratch (incremental: the group
-        // the update starts in)
-        const uint64_t gbase = INC ? (((sp.chunk0 << 6) >> (3 * lvl)) >> 3) : 0;
-        const uint64_t slot = sp.grp0 + goff + (g - gbase);
-        unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
-        if (x < k) {
-          uint64_t a0 = v0, a1 = v1;
-          if (pos < 7) {
-            const uint64_t key = tree_key<W>(P, x, lvl, pos);
-            a0 = nh64(v0, key);
-            a1 = nh64(v1, key);
-          }
-          atomicAdd(acc, (unsigned long long)a0);
-          atomicAdd(acc + 1, (unsigned long long)a1);
-        }
-        __threadfence();
-        __syncwarp();
-        unsigned old = 0;
-        if (ln == 0) old = atomicAdd(P.scr.grp_cnt + slot, 1u);
-        old = __shfl_sync(kFull, old, 0);
-        if (old != kFan - 1) break;
-        // eighth arrival: the parent node is complete and ours
-        __threadfence();
-        if (x < k) {
-          v0 = ld_cg(acc);
-          v1 = ld_cg(acc + 1);
-          acc[0] = 0;
-          acc[1] = 0;
-        }
-        if (ln == 0) P.scr.grp_cnt[slot] = 0;
-        goff += (C >> 3) - gbase;
-        lvl += 1;
-        idx = g;
-      }
+        if (x == t)
+          pend[t] += nh64(v0, final_key<W>(P, t, lvl, j, 2 * p)) +
+                     nh64(v1, final_key<W>(P, t, lvl, j, 2 * p + 1));
+      anyp = true;
     }
+    return kNoNode;
   }
-  if constexpr (INC) return;  // nothing is final before the string ends
+  const int pos = (int)(idx & 7);
+  const uint64_t slot = sp.grp0 + goff + ((idx >> 3) - group_base<INC>(sp, lvl));
+  if (x < k) {
+    unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
+    uint64_t a0 = v0, a1 = v1;
+    if (pos < 7) {
+      const uint64_t key = tree_key<W>(P, x, lvl, pos);
+      a0 = nh64(v0, key);
+      a1 = nh64(v1, key);
+    }
+    atomicAdd(acc, (unsigned long long)a0);
+    atomicAdd(acc + 1, (unsigned long long)a1);
+  }
+  return slot;
+}
 
-  griddep_wait();
+// Counts one arrival at a group after a fence that makes this warp's
+// contributions visible; returns the previous count (all lanes).
+__device__ __forceinline__ unsigned arrive(const KParams &P, uint64_t slot, int ln) {
+  __threadfence();
+  __syncwarp();
+  unsigned old = 0;
+  if (ln == 0) old = atomicAdd(P.scr.grp_cnt + slot, 1u);
+  return __shfl_sync(kFull, old, 0);
+}
+
+// The warp that made the eighth arrival takes the group's node (its
+// accumulator, then cleared for the next launch) into (v0, v1).
+template <int W>
+__device__ __forceinline__ void take_group(const KParams &P, uint64_t slot, int ln, uint64_t &v0, uint64_t &v1) {
+  constexpr int k = Spec<W>::k;
+  const int x = ln >> 2, p = ln & 3;
+  __threadfence();
+  if (x < k) {
+    unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
+    v0 = ld_cg(acc);
+    v1 = ld_cg(acc + 1);
+    acc[0] = 0;
+    acc[1] = 0;
+  }
+  if (ln == 0) P.scr.grp_cnt[slot] = 0;
+}
+
+// Carries node idx of level lvl up the tree, waiting at every level: as long
+// as this warp's arrival completes a group, it takes the parent node and goes
+// on one level up.
+template <int W, bool INC>
+__device__ void climb(const KParams &P, const StrPlan &sp, int lvl, uint64_t idx, uint64_t goff,
+                      uint64_t v0, uint64_t v1, int ln, uint64_t (&pend)[Spec<W>::k], bool &anyp) {
+  for (;;) {
+    const uint64_t slot = add_node<W, INC>(P, sp, lvl, idx, goff, v0, v1, ln, pend, anyp);
+    if (slot == kNoNode) return;
+    if (arrive(P, slot, ln) != kFan - 1) return;
+    take_group<W>(P, slot, ln, v0, v1);
+    goff = next_goff<INC>(sp, lvl, goff);
+    lvl += 1;
+    idx >>= 3;
+  }
+}
+
+// Adds this warp's share of a string's final-NH sum into the string's sum.
+template <int W>
+__device__ __forceinline__ void flush_pending(const KParams &P, unsigned sidx, uint64_t (&pend)[Spec<W>::k],
+                                              bool anyp, int ln) {
+  constexpr int k = Spec<W>::k;
   if (__any_sync(kFull, anyp)) {
 #pragma unroll
     for (int t = 0; t < k; ++t) pend[t] = warp_sum(pend[t]);
@@ -479,12 +525,64 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx,
       for (int t = 0; t < k; ++t)
         if (pend[t]) atomicAdd(P.scr.str_acc + (uint64_t)sidx * k + t, (unsigned long long)pend[t]);
   }
+}
+
+// One chunk of a batch: its levels, the climb, and the string's completion
+// count (the warp that completes the string runs the finaliser).
+template <int W, int L, bool ALIGNED>
+__device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, uint64_t c, int ln) {
+  constexpr int k = Spec<W>::k;
+  uint64_t pend[k];  // this thread's share of the final-NH sum
+#pragma unroll
+  for (int t = 0; t < k; ++t) pend[t] = 0;
+  bool anyp = false;
+  uint64_t v0, v1;
+  const bool full = chunk_root<W, L, ALIGNED>(P, sp, c, ln, pend, anyp, v0, v1);
+  griddep_wait();
+  if (full) climb<W, false>(P, sp, L, c, 0, v0, v1, ln, pend, anyp);
+  flush_pending<W>(P, sidx, pend, anyp, ln);
   __threadfence();
   __syncwarp();
   unsigned old = 0;
   if (ln == 0) old = atomicAdd(P.scr.str_done + sidx, 1u);
   old = __shfl_sync(kFull, old, 0);
   if (old == sp.n_items - 1) finish_string<W>(P, sp, sidx, ln);
+}
+
+// A warp's share of one string (single-string launches, incremental updates):
+// chunks from the cursor, each root climbing as far as this warp completes
+// groups.  Completion of the string needs no count per chunk (a fence and an
+// L2 round trip the warp would wait on): the last warp to leave the launch
+// that ends the string runs the finaliser.
+template <int W, int L, bool ALIGNED, bool INC>
+__device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int ln) {
+  constexpr int k = Spec<W>::k;
+  const StrPlan &sp = P.single;
+  bool first = true;
+  for (;;) {
+    unsigned long long item = 0;
+    if (first) {
+      // each warp's first chunk is fixed, so it can be hashed before an
+      // overlapping launch's predecessor has finished with the scratch
+      item = P.item_begin + gw;
+      first = false;
+    } else {
+      if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
+      item = __shfl_sync(kFull, item, 0) + P.item_begin + P.total_warps;
+    }
+    if (item >= P.item_end) break;
+    uint64_t pend[k];  // this thread's share of the final-NH sum
+#pragma unroll
+    for (int t = 0; t < k; ++t) pend[t] = 0;
+    bool anyp = false;
+    uint64_t v0, v1;
+    const bool full = chunk_root<W, L, ALIGNED>(P, sp, item, ln, pend, anyp, v0, v1);
+    // everything below touches the scratch: an overlapping launch must first
+    // see its predecessor finish
+    griddep_wait();
+    if (full) climb<W, INC>(P, sp, L, item, 0, v0, v1, ln, pend, anyp);
+    flush_pending<W>(P, 0, pend, anyp, ln);
+  }
 }
 
 // ---- the persistent kernel ----------------------------------------------------
@@ -499,28 +597,39 @@ __device__ __forceinline__ unsigned find_string(const unsigned long long *item0s
   return lo;
 }
 
-__device__ __forceinline__ void exit_protocol(const KParams &P, int ln) {
+// Every warp passes here on leaving; the last one (all other warps' work is
+// then visible to it) rearms the cursor for the next launch and learns that
+// it was last.
+__device__ __forceinline__ bool exit_protocol(const KParams &P, int ln) {
   griddep_wait();
   __syncwarp();
+  unsigned old = 0;
   if (ln == 0) {
     __threadfence();
-    const unsigned old = atomicAdd(&P.scr.ctl->exit, 1u);
+    old = atomicAdd(&P.scr.ctl->exit, 1u);
     if (old == P.total_warps - 1) {
-      // every warp has made its last grab: rearm for the next launch
       P.scr.ctl->cursor = 0;
       P.scr.ctl->exit = 0;
       __threadfence();
     }
   }
+  return __shfl_sync(kFull, old, 0) == P.total_warps - 1;
 }
 
 template <int W, int L, bool SINGLE, bool ALIGNED, bool INC = false>
 __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KParams P) {
-  static_assert(!INC || SINGLE, "incremental updates hash one string");
+  static_assert(!INC || (SINGLE && L == 2), "incremental updates hash one string in 64-execution chunks");
   const int ln = threadIdx.x & 31;
-  uint64_t total;
-  if (SINGLE) {
-    total = P.item_end;
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if constexpr (SINGLE) {
+    griddep_launch_dependents();
+    single_string<W, L, ALIGNED, INC>(P, gw, ln);
+    const bool last = exit_protocol(P, ln);
+    // nothing is final in an incremental update; a string hashed over several
+    // launches ends with the launch that reaches its item count (parts of a
+    // split string set an unreachable count: they are finished elsewhere)
+    if (!INC && last && P.item_end >= P.single.n_items) finish_string<W>(P, P.single, 0, ln);
+    return;
   } else {
     // a batch runs an aligned-only and a general variant; the planner's
     // alignment flag selects one, the other leaves at once
@@ -528,28 +637,12 @@ __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KP
       exit_protocol(P, ln);
       return;
     }
-    total = __ldcg(&P.scr.ctl->total);
-  }
-  // single string: each warp's first chunk is fixed (chunk = warp index), so
-  // it can be hashed before the scratch may be touched; later chunks come
-  // from the cursor
-  if (SINGLE) griddep_launch_dependents();
-  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  bool first = SINGLE;
-  for (;;) {
-    unsigned long long item = 0;
-    if (first) {
-      item = P.item_begin + gw;
-      first = false;
-    } else {
+    const uint64_t total = __ldcg(&P.scr.ctl->total);
+    for (;;) {
+      unsigned long long item = 0;
       if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
       item = __shfl_sync(kFull, item, 0);
-      if (SINGLE) item += P.item_begin + P.total_warps;
-    }
-    if (item >= total) break;
-    if (SINGLE) {
-      hash_chunk<W, L, ALIGNED, INC>(P, P.single, 0, item, ln);
-    } else {
+      if (item >= total) break;
       const unsigned s = find_string(P.item0s, P.count, item);
       const StrPlan sp = P.plans[s];
       const uint64_t c = item - sp.item0;
@@ -558,8 +651,8 @@ __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KP
       else
         hash_chunk<W, L, false>(P, sp, s, c, ln);
     }
+    exit_protocol(P, ln);
   }
-  exit_protocol(P, ln);
 }
 
 // ---- the batch planner (one block) ---------------------------------------------
