@@ -40,17 +40,6 @@ uint64_t groups_for_update(uint64_t C, uint64_t M) {
   return g;
 }
 
-// Whether some level's incomplete group holds stack nodes (d > 0) and is
-// completed by the update, so its accumulator must be seeded first.
-bool needs_seed(uint64_t C, uint64_t M) {
-  const uint64_t N0 = C * kChunkExecs, N1 = (C + M) * kChunkExecs;
-  for (int lvl = 2; lvl < kLevels - 1; ++lvl) {
-    const uint64_t n0 = N0 >> (3 * lvl), n1 = N1 >> (3 * lvl);
-    if ((n0 & 7) && (n1 >> 3) > (n0 >> 3)) return true;
-  }
-  return false;
-}
-
 uint64_t seed_fingerprint(const ht_ctx *c) {
   uint64_t h = 0xcbf29ce484222325ull;  // FNV-1a over the seed words' bytes
   for (uint64_t w : c->h_seeds)
@@ -74,7 +63,8 @@ struct ht_inc {
   unsigned long long *str_acc = nullptr;
   unsigned int *str_done = nullptr;
   Ctl *ctl = nullptr;
-  unsigned long long *stack = nullptr;
+  unsigned long long *stack[2] = {nullptr, nullptr};  // the state and the next update's output
+  int cur = 0;            // stack[cur] holds the state
   uint8_t *buf = nullptr;
   // host mirror of the counter
   uint64_t chunks = 0;  // whole chunks hashed
@@ -100,12 +90,15 @@ void inc_params(const ht_inc *h, KParams &P) {
   P.scr.str_done = h->str_done;
   P.scr.ctl = h->ctl;
   P.scr.cap_groups = h->cap_groups;
-  P.stack = h->stack;
+  P.stack = h->stack[h->cur];
+  P.stack_in = h->stack[h->cur];
   P.count = 1;
 }
 
-// Hashes chunks [h->chunks, h->chunks + M) found at ptr (device).
-int run_chunks(ht_inc *h, const uint8_t *ptr, uint64_t M, cudaStream_t s) {
+// Hashes chunks [h->chunks, h->chunks + M): the first from the chunk buffer
+// if first_from_buf, the others (or all) contiguous at ptr (device).  One
+// launch; it reads the stack of the state and writes the other one.
+int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, cudaStream_t s) {
   ht_ctx *c = h->ctx;
   const KernelSet &ks = *c->ks;
   const uint64_t C = h->chunks;
@@ -113,22 +106,20 @@ int run_chunks(ht_inc *h, const uint8_t *ptr, uint64_t M, cudaStream_t s) {
     return set_error(HT_ERR_ARG, "incremental update needs more group slots than reserved");
   KParams P;
   inc_params(h, P);
+  P.stack_in = h->stack[h->cur];
+  P.stack = h->stack[h->cur ^ 1];
   StrPlan &sp = P.single;
-  sp.ptr = ptr - C * h->granule;  // the kernel addresses the string from its start
+  // the kernel addresses the string from its start
+  sp.ptr = ptr - (C + (first_from_buf ? 1 : 0)) * h->granule;
+  if (first_from_buf) P.inc_first = h->buf;
   sp.n_exec = (C + M) * kChunkExecs;
   sp.len = sp.n_exec * (uint64_t)ks.exec_bytes;
   sp.chunk0 = C;
   sp.n_items = 0xffffffffu;
   void *args[] = {&P};
-  cudaError_t e;
-  if (needs_seed(C, M)) {
-    e = cudaLaunchKernel(ks.inc_seed, dim3(1), dim3(32), args, 0, s);
-    if (e != cudaSuccess) return cuda_error(e, "incremental seed launch");
-    c->launches.fetch_add(1);
-  }
   const void *func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.inc_aligned : ks.inc_unaligned;
   int bps = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, func, kTpb, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, func, kTpb, 0);
   if (e != cudaSuccess) return cuda_error(e, "occupancy");
   bps = std::max(1, std::min(bps, 2));
   const uint64_t wpb = kTpb / 32;
@@ -144,6 +135,7 @@ int run_chunks(ht_inc *h, const uint8_t *ptr, uint64_t M, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_error(e, "incremental update launch");
   c->launches.fetch_add(1);
   h->chunks = C + M;
+  h->cur ^= 1;
   return HT_OK;
 }
 
@@ -153,7 +145,8 @@ void free_inc(ht_inc *h) {
   cudaFree(h->str_acc);
   cudaFree(h->str_done);
   cudaFree(h->ctl);
-  cudaFree(h->stack);
+  cudaFree(h->stack[0]);
+  cudaFree(h->stack[1]);
   cudaFree(h->buf);
   for (int i = 0; i < kStageSlots2; ++i) {
     cudaFree(h->stage[i]);
@@ -190,7 +183,8 @@ int ht_inc_create(ht_ctx *c, ht_inc **out) {
   alloc((void **)&h->str_acc, 8 * sizeof(unsigned long long));
   alloc((void **)&h->str_done, 256);
   alloc((void **)&h->ctl, sizeof(Ctl));
-  alloc((void **)&h->stack, stack_words(h) * sizeof(unsigned long long));
+  alloc((void **)&h->stack[0], stack_words(h) * sizeof(unsigned long long));
+  alloc((void **)&h->stack[1], stack_words(h) * sizeof(unsigned long long));
   alloc((void **)&h->buf, h->granule);
   if (e != cudaSuccess) {
     free_inc(h);
@@ -246,6 +240,7 @@ int ht_inc_update(ht_inc *h, const void *data_dev, uint64_t len, ht_stream_t str
   cudaStream_t s = (cudaStream_t)stream;
   const uint8_t *p = static_cast<const uint8_t *>(data_dev);
   uint64_t m = len;
+  bool buffered = false;  // the chunk buffer holds a whole chunk for the first launch
   if (h->fill) {
     // complete the buffered chunk first
     const uint64_t r = std::min(m, h->granule - h->fill);
@@ -254,15 +249,15 @@ int ht_inc_update(ht_inc *h, const void *data_dev, uint64_t len, ht_stream_t str
     p += r;
     m -= r;
     if (h->fill < h->granule) return HT_OK;
-    const int rc = run_chunks(h, h->buf, 1, s);
-    if (rc) return rc;
-    h->fill = 0;
+    buffered = true;
   }
   uint64_t M = m / h->granule;
-  while (M) {
-    const uint64_t piece = std::min(M, kMaxChunks);
-    const int rc = run_chunks(h, p, piece, s);
+  while (buffered || M) {
+    const uint64_t piece = std::min(M, kMaxChunks - (buffered ? 1 : 0));
+    const int rc = run_chunks(h, buffered, p, piece + (buffered ? 1 : 0), s);
     if (rc) return rc;
+    if (buffered) h->fill = 0;
+    buffered = false;
     p += piece * h->granule;
     m -= piece * h->granule;
     M -= piece;
@@ -282,16 +277,18 @@ int ht_inc_update_host(ht_inc *h, const void *data_host, uint64_t len, ht_stream
   cudaStream_t s = (cudaStream_t)stream;
   const uint8_t *p = static_cast<const uint8_t *>(data_host);
   uint64_t m = len;
+  bool buffered = false;  // the chunk buffer holds a whole chunk for the first launch
   if (h->fill) {
     const uint64_t r = std::min(m, h->granule - h->fill);
     if (r) INC_CUDA(cudaMemcpyAsync(h->buf + h->fill, p, r, cudaMemcpyHostToDevice, s));
     h->fill += r;
     p += r;
     m -= r;
-    if (h->fill < h->granule) return HT_OK;
-    const int rc = run_chunks(h, h->buf, 1, s);
-    if (rc) return rc;
-    h->fill = 0;
+    if (h->fill < h->granule) {
+      INC_CUDA(cudaStreamSynchronize(s));
+      return HT_OK;
+    }
+    buffered = true;
   }
   uint64_t M = m / h->granule;
   if (M) {
@@ -311,13 +308,20 @@ int ht_inc_update_host(ht_inc *h, const void *data_host, uint64_t len, ht_stream
       INC_CUDA(cudaMemcpyAsync(h->stage[slot], p, piece * h->granule, cudaMemcpyHostToDevice, h->copy_stream));
       INC_CUDA(cudaEventRecord(h->ev_copy[slot], h->copy_stream));
       INC_CUDA(cudaStreamWaitEvent(s, h->ev_copy[slot], 0));
-      const int rc = run_chunks(h, h->stage[slot], piece, s);
+      const int rc = run_chunks(h, buffered, h->stage[slot], piece + (buffered ? 1 : 0), s);
       if (rc) return rc;
       INC_CUDA(cudaEventRecord(h->ev_hash[slot], s));
+      if (buffered) h->fill = 0;
+      buffered = false;
       p += piece * h->granule;
       m -= piece * h->granule;
       M -= piece;
     }
+  }
+  if (buffered) {
+    const int rc = run_chunks(h, true, h->buf, 1, s);
+    if (rc) return rc;
+    h->fill = 0;
   }
   if (m) {
     INC_CUDA(cudaMemcpyAsync(h->buf, p, m, cudaMemcpyHostToDevice, s));
@@ -375,7 +379,7 @@ int ht_inc_export(const ht_inc *h, void *state_host, size_t n, ht_stream_t strea
   hd[2] = h->chunks;
   hd[3] = h->fill;
   uint8_t *b = static_cast<uint8_t *>(state_host) + 4 * sizeof(uint64_t);
-  INC_CUDA(cudaMemcpyAsync(b, h->stack, stack_words(h) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  INC_CUDA(cudaMemcpyAsync(b, h->stack[h->cur], stack_words(h) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   if (h->fill)
     INC_CUDA(cudaMemcpyAsync(b + stack_words(h) * sizeof(uint64_t), h->buf, h->fill, cudaMemcpyDeviceToHost, s));
   INC_CUDA(cudaStreamSynchronize(s));
@@ -396,7 +400,7 @@ int ht_inc_import(ht_inc *h, const void *state_host, size_t n, ht_stream_t strea
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const uint8_t *b = static_cast<const uint8_t *>(state_host) + 4 * sizeof(uint64_t);
-  INC_CUDA(cudaMemcpyAsync(h->stack, b, stack_words(h) * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  INC_CUDA(cudaMemcpyAsync(h->stack[h->cur], b, stack_words(h) * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   if (hd[3])
     INC_CUDA(cudaMemcpyAsync(h->buf, b + stack_words(h) * sizeof(uint64_t), hd[3], cudaMemcpyHostToDevice, s));
   INC_CUDA(cudaStreamSynchronize(s));

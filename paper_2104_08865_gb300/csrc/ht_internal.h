@@ -66,7 +66,9 @@ struct KParams {
   const unsigned long long *chunk0s;  // batch mode: chunk0 of each string (+ total)
   const unsigned long long *unitb0s;  // batch mode: unitb0 of each string (+ total)
   unsigned long long *digests;  // count * k words
-  unsigned long long *stack;    // incremental mode: pending nodes [level][8][k][8]
+  unsigned long long *stack;    // incremental mode: pending nodes [level][8][k][8] (written)
+  const unsigned long long *stack_in;  // incremental mode: the previous update's stack (read)
+  const uint8_t *inc_first;     // incremental mode: bytes of chunk chunk0 if not at ptr (else null)
   StrPlan single;               // single-string mode: the string
   unsigned long long item_begin, item_end;  // single mode: item range of this launch
   unsigned int count;           // batch mode: strings
@@ -107,7 +109,6 @@ struct KernelSet {
   const void *part_finish;  // parts: climb merged groups, write the digest
   const void *inc_aligned;    // incremental: whole chunks of one update
   const void *inc_unaligned;
-  const void *inc_seed;       // incremental: frontier groups from the stack
   const void *inc_stack;      // incremental: pending stack nodes into the sum
   int exec_bytes, k, n_seed, off_T, off_F, off_R, ew;
 };

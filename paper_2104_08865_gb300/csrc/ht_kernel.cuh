@@ -264,23 +264,23 @@ __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx
 
 constexpr uint64_t kNoNode = ~0ull;
 
-// Levels 0..L of chunk c of a string (Section 5.2 tree, Eq. stack-construction):
-// the EHC values of its executions, level 1 in registers, level 2 across the
+// Levels 0..L of chunk c of a string (Section 5.2 tree, Eq. stack-construction)
+// whose bytes start at base: the EHC values of its executions, level 1 in registers, level 2 across the
 // eight x-threads, level 3 over eight sub-chunks (L = 3).  A full chunk's root
 // (node c of level L) is returned in (v0, v1) of thread x < k (tree x, lanes
 // 2p and 2p+1); the leaves and nodes of the string's last, incomplete chunk
 // are pending roots, whose final NH goes into pend.  Returns whether the
 // chunk is full.  Touches no scratch.
 template <int W, int L, bool ALIGNED>
-__device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, uint64_t c, int ln,
-                                           uint64_t (&pend)[Spec<W>::k], bool &anyp,
+__device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, const uint8_t *base,
+                                           uint64_t c, int ln, uint64_t (&pend)[Spec<W>::k], bool &anyp,
                                            uint64_t &v0, uint64_t &v1) {
   constexpr int k = Spec<W>::k;
   constexpr uint64_t B = Dims<W>::exec_bytes;
   constexpr uint64_t CH = 1ull << (3 * L);
   const int x = ln >> 2, p = ln & 3;
   const uint64_t N = sp.n_exec;
-  const uint32_t sh = ALIGNED ? 0u : (uint32_t)(((uintptr_t)sp.ptr) & 15u);
+  const uint32_t sh = ALIGNED ? 0u : (uint32_t)(((uintptr_t)base) & 15u);
   const bool full = c * CH < N && (N - c * CH) >= CH;
   const uint64_t e0 = c * CH;
   if (e0 >= N) return false;
@@ -294,7 +294,7 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
       // eight executions, one per x-thread; level 1 across the x-threads
       const int m = (int)((N - e0) < 8 ? (N - e0) : 8);
       uint64_t y[2][k];
-      if (x < m) ehc2<W, ALIGNED>(sp.ptr + (e0 + (uint64_t)x) * B, p, sh, P, y);
+      if (x < m) ehc2<W, ALIGNED>(base + (e0 + (uint64_t)x) * B, p, sh, P, y);
       if (full) {
 #pragma unroll
         for (int t = 0; t < k; ++t) {
@@ -324,7 +324,7 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
       for (int l = 0; l < 2; ++l)
 #pragma unroll
         for (int t = 0; t < k; ++t) n1[l][t] = 0;
-      const uint8_t *ex = sp.ptr + (sb + 8ull * x) * B;
+      const uint8_t *ex = base + (sb + 8ull * x) * B;
       if (cnt == 8) {
         // eight leaves -> one level-1 node per (tree, lane), in registers;
         // two executions per iteration keep two loads batches in flight
@@ -468,14 +468,15 @@ __device__ __forceinline__ uint64_t add_node(const KParams &P, const StrPlan &sp
   return slot;
 }
 
-// Counts one arrival at a group after a fence that makes this warp's
-// contributions visible; returns the previous count (all lanes).
-__device__ __forceinline__ unsigned arrive(const KParams &P, uint64_t slot, int ln) {
+// Counts n arrivals at a group (n children's contributions) after a fence
+// that makes this warp's contributions visible; returns the count after
+// them (all lanes).  The arrival that brings it to 8 completes the group.
+__device__ __forceinline__ unsigned arrive(const KParams &P, uint64_t slot, int ln, unsigned n = 1) {
   __threadfence();
   __syncwarp();
   unsigned old = 0;
-  if (ln == 0) old = atomicAdd(P.scr.grp_cnt + slot, 1u);
-  return __shfl_sync(kFull, old, 0);
+  if (ln == 0) old = atomicAdd(P.scr.grp_cnt + slot, n);
+  return __shfl_sync(kFull, old, 0) + n;
 }
 
 // The warp that made the eighth arrival takes the group's node (its
@@ -504,7 +505,7 @@ __device__ void climb(const KParams &P, const StrPlan &sp, int lvl, uint64_t idx
   for (;;) {
     const uint64_t slot = add_node<W, INC>(P, sp, lvl, idx, goff, v0, v1, ln, pend, anyp);
     if (slot == kNoNode) return;
-    if (arrive(P, slot, ln) != kFan - 1) return;
+    if (arrive(P, slot, ln) != kFan) return;
     take_group<W>(P, slot, ln, v0, v1);
     goff = next_goff<INC>(sp, lvl, goff);
     lvl += 1;
@@ -537,7 +538,7 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, u
   for (int t = 0; t < k; ++t) pend[t] = 0;
   bool anyp = false;
   uint64_t v0, v1;
-  const bool full = chunk_root<W, L, ALIGNED>(P, sp, c, ln, pend, anyp, v0, v1);
+  const bool full = chunk_root<W, L, ALIGNED>(P, sp, sp.ptr, c, ln, pend, anyp, v0, v1);
   griddep_wait();
   if (full) climb<W, false>(P, sp, L, c, 0, v0, v1, ln, pend, anyp);
   flush_pending<W>(P, sidx, pend, anyp, ln);
@@ -549,14 +550,69 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, u
   if (old == sp.n_items - 1) finish_string<W>(P, sp, sidx, ln);
 }
 
+// Incremental update, one warp: the stack carries, for every level, the
+// nodes of its last, incomplete group (d of them).  If the update completes
+// that group, the d nodes enter it as one arrival of d children (the sum of
+// their tree-key NH terms); arrivals are sums and counts, so the order
+// against the chunks' own arrivals does not matter, and whichever brings the
+// count to 8 takes the parent node and climbs on.  Otherwise the d nodes stay
+// pending and are copied to the same positions of the new stack (the
+// update's own pending nodes of that level come after them).  The previous
+// stack is only read, so no other warp's writes can race with this.
+template <int W>
+__device__ void seed_frontier(const KParams &P, const StrPlan &sp, int ln) {
+  constexpr int k = Spec<W>::k;
+  const int x = ln >> 2, p = ln & 3;
+  const uint64_t N0 = sp.chunk0 << 6, N1 = sp.n_exec;
+  uint64_t goff = 0;
+  for (int lvl = 2; lvl < kLevels; ++lvl) {
+    const uint64_t n0 = N0 >> (3 * lvl), n1 = N1 >> (3 * lvl);
+    const unsigned d = (unsigned)(n0 & 7);
+    const bool completes = (n1 >> 3) > (n0 >> 3);
+    if (d && !completes) {
+      if (x < k)
+        for (unsigned j = 0; j < d; ++j) {
+          const uint64_t o = (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
+          P.stack[o] = P.stack_in[o];
+          P.stack[o + 1] = P.stack_in[o + 1];
+        }
+    } else if (d) {
+      const uint64_t slot = sp.grp0 + goff;  // the level's first group slot
+      if (x < k) {
+        uint64_t a0 = 0, a1 = 0;
+        for (unsigned j = 0; j < d; ++j) {  // j < 7: every stack node is hashed
+          const uint64_t key = tree_key<W>(P, x, lvl, (int)j);
+          const uint64_t o = (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
+          a0 += nh64(P.stack_in[o], key);
+          a1 += nh64(P.stack_in[o + 1], key);
+        }
+        unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
+        atomicAdd(acc, (unsigned long long)a0);
+        atomicAdd(acc + 1, (unsigned long long)a1);
+      }
+      if (arrive(P, slot, ln, d) == kFan) {
+        uint64_t pend[k];  // (unused: incremental pending nodes go to the stack)
+        bool anyp = false;
+        uint64_t v0 = 0, v1 = 0;
+        take_group<W>(P, slot, ln, v0, v1);
+        climb<W, true>(P, sp, lvl + 1, n0 >> 3, next_goff<true>(sp, lvl, goff), v0, v1, ln, pend, anyp);
+      }
+    }
+    if (lvl < kLevels - 1) goff = next_goff<true>(sp, lvl, goff);
+  }
+}
+
 // A warp's share of one string (single-string launches, incremental updates):
 // chunks from the cursor, each root climbing as far as this warp completes
 // groups.  Completion of the string needs no count per chunk (a fence and an
 // L2 round trip the warp would wait on): the last warp to leave the launch
-// that ends the string runs the finaliser.
+// that ends the string runs the finaliser.  An incremental update may take
+// its first chunk from the buffer of bytes carried over from earlier updates
+// (P.inc_first), and its first warp seeds the frontier groups.
 template <int W, int L, bool ALIGNED, bool INC>
 __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int ln) {
   constexpr int k = Spec<W>::k;
+  constexpr uint64_t G = (1ull << (3 * L)) * Dims<W>::exec_bytes;
   const StrPlan &sp = P.single;
   bool first = true;
   for (;;) {
@@ -576,12 +632,20 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
     for (int t = 0; t < k; ++t) pend[t] = 0;
     bool anyp = false;
     uint64_t v0, v1;
-    const bool full = chunk_root<W, L, ALIGNED>(P, sp, item, ln, pend, anyp, v0, v1);
+    const uint8_t *base = sp.ptr;
+    if constexpr (INC) {
+      if (P.inc_first && item == sp.chunk0) base = P.inc_first - item * G;
+    }
+    const bool full = chunk_root<W, L, ALIGNED>(P, sp, base, item, ln, pend, anyp, v0, v1);
     // everything below touches the scratch: an overlapping launch must first
     // see its predecessor finish
     griddep_wait();
     if (full) climb<W, INC>(P, sp, L, item, 0, v0, v1, ln, pend, anyp);
     flush_pending<W>(P, 0, pend, anyp, ln);
+  }
+  griddep_wait();
+  if constexpr (INC) {
+    if (gw == 0) seed_frontier<W>(P, sp, ln);
   }
 }
 

@@ -265,7 +265,6 @@ KernelSet make_kernel_set() {
   ks.part_finish = (const void *)part_finish_kernel<W, 2>;
   ks.inc_aligned = (const void *)hash_kernel<W, 2, true, true, true>;
   ks.inc_unaligned = (const void *)hash_kernel<W, 2, true, false, true>;
-  ks.inc_seed = (const void *)inc_seed_kernel<W>;
   ks.inc_stack = (const void *)inc_stack_kernel<W>;
   ks.exec_bytes = Dims<W>::exec_bytes;
   ks.k = Spec<W>::k;
