@@ -286,6 +286,66 @@ def run_batch(args, dev, stream):
             "digests_equal": same}
 
 
+def run_dedup(args, dev, stream):
+    """Deduplication by content: the batch of 50,000 strings (log-uniform
+    64 B .. 1 MiB, splitmix64 seed 3, width 24) plus 12,500 entries aliasing
+    earlier strings' bytes, hashed in one batch launch and inserted into the
+    digest table (representatives out).  Times the whole chain against the
+    hashing alone; the representatives must be what the construction fixes
+    (each original its own, each alias its original)."""
+    import numpy as np
+    import torch
+
+    from paper_2104_08865_gb300 import Hasher, Table, abi, inputs
+    lens = inputs.log_uniform_lengths(3, args.batch_strings, 64, 1 << 20)
+    offs, total = _aligned_offsets(lens)
+    buf = inputs.stream_bytes_torch(3, 0, total + 256, dev)
+    rng = np.random.default_rng(8)
+    alias = rng.integers(0, len(lens), len(lens) // 4)
+    all_offs = np.concatenate([offs, offs[alias]])
+    all_lens = np.concatenate([lens, lens[alias]])
+    n = len(all_lens)
+    ptrs = torch.tensor(buf.data_ptr() + all_offs, dtype=torch.int64, device=dev)
+    lt = torch.tensor(all_lens, dtype=torch.int64, device=dev)
+    h = Hasher(24, seed_words=abi.ht_seed_expand(SEED_KEY, 24))
+    abi.ht_ctx_reserve(h.ctx, int(all_lens.sum()) + (1 << 20), n)
+    dig = torch.empty((n, 3), dtype=torch.int64, device=dev)
+    rep = torch.empty(n, dtype=torch.int32, device=dev)
+    t = Table(h, max_entries=n, seed64=0x7AB1E)
+
+    def chain():
+        abi.ht_hash_batch(h.ctx, ptrs, lt, n, dig, stream)
+        t.clear(stream)
+        abi.ht_table_insert(t.t, dig, n, rep, stream)
+
+    for _ in range(3):
+        chain()
+    torch.cuda.synchronize()
+    t.status()
+    got = rep.cpu().numpy().view(np.uint32).astype(np.int64)
+    ok = bool(np.array_equal(got[:len(lens)], np.arange(len(lens))) and np.array_equal(got[len(lens):], alias))
+    reps = 10
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(reps):
+        abi.ht_hash_batch(h.ctx, ptrs, lt, n, dig, stream)
+    e1.record(stream)
+    for _ in range(reps):
+        chain()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    ms_hash = e0.elapsed_time(e1) / reps
+    ms_chain = e1.elapsed_time(e2) / reps
+    nbytes = int(all_lens.sum())
+    t.close()
+    h.close()
+    return {"workload": "%d strings (%d distinct, log-uniform 64 B..1 MiB), %.2f GB, width 24" % (
+                n, len(lens), nbytes / 1e9),
+            "chain_gbs": round(nbytes / ms_chain / 1e6, 1), "chain_ms": round(ms_chain, 3),
+            "hash_only_ms": round(ms_hash, 3), "table_ms": round(ms_chain - ms_hash, 3),
+            "distinct": int((got == np.arange(n)).sum()), "representatives_ok": ok}
+
+
 def run_incremental(args, dev, stream, data, want):
     """The benchmark's string hashed incrementally at width 24 (init / update /
     final): device-resident pieces of 64 MiB and of 1 MiB + 3 bytes (every
@@ -546,6 +606,7 @@ def run_gpu(args):
     batch = run_batch(args, dev, stream) if not args.no_batch else None
     incremental = (run_incremental(args, dev, stream, data, digests[24])
                    if (rank == 0 and not args.no_inc) else None)
+    dedup = run_dedup(args, dev, stream) if (rank == 0 and not args.no_dedup) else None
     serving = run_serving(args, dev, stream) if (rank == 0 and not args.no_serve) else None
 
     if rank == 0:
@@ -570,7 +631,7 @@ def run_gpu(args):
                          "peak_source": peak_kind},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": ck,
             "shapes": shapes,
-            "batch": batch, "incremental": incremental, "serving": serving,
+            "batch": batch, "incremental": incremental, "dedup": dedup, "serving": serving,
             "digests": {str(w): ["%016x" % v for v in digests[w]] for w in WIDTHS},
         }
         print(json.dumps(line), flush=True)
@@ -600,6 +661,7 @@ def main():
                     help="time the step without overlapping consecutive launches")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-inc", action="store_true", help="skip the incremental-hashing leg")
+    ap.add_argument("--no-dedup", action="store_true", help="skip the deduplication leg")
     ap.add_argument("--batch-strings", type=int, default=50_000)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0)

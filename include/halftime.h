@@ -37,6 +37,7 @@ typedef struct CUstream_st *ht_stream_t; /* same type as cudaStream_t */
 typedef struct ht_ctx ht_ctx;
 typedef struct ht_server ht_server;
 typedef struct ht_inc ht_inc;
+typedef struct ht_table ht_table;
 
 /* ---- status codes -------------------------------------------------------- */
 #define HT_OK 0
@@ -281,6 +282,68 @@ int ht_inc_export(const ht_inc *h, void *state_host, size_t n, ht_stream_t strea
  * Errors: HT_ERR_ARG (short buffer, other width or seed words, corrupt
  * header), HT_ERR_CUDA. */
 int ht_inc_import(ht_inc *h, const void *state_host, size_t n, ht_stream_t stream);
+
+/* ---- long strings in a hash table by their digests ---------------------------
+ * HalftimeHash is a universe-collapsing family (Section 1): it maps long
+ * strings to short digests that a family made for short inputs can hash as
+ * if they were the strings, and almost universality composes (the two
+ * collision bounds add up: the composition lemma, Section 5.2).  An
+ * ht_table keys strings by their digests on the device: entries are digests
+ * numbered by insertion (ids 0, 1, ...); the first slot probed is the top
+ * bits of a vector multiply-shift hash of the digest's 32-bit halves,
+ *   h(x) = (a_0 + sum_i a_{i+1} x_i) mod 2^64,  x_0 = low half of word 0,
+ *   x_1 = its high half, x_2 = low half of word 1, ...,
+ * with keys a_0 .. a_2k the splitmix64 outputs of the table's seed (strongly
+ * universal in its top l <= 33 bits); collisions probe linearly.  A slot
+ * holds the smallest id of the entries with its digest, so inserting a batch
+ * gives every entry's representative (deduplication by content) and a find
+ * gives the id of an equal entry (a join).  Two different strings share a
+ * digest with the probability bounded in Section 5 (about 2^-60 or less per
+ * pair): then they are treated as equal.
+ *   - The table holds at most max_entries entries and is at most half full
+ *     (2^m >= 2 max_entries slots of 4 bytes, plus 8k bytes per entry).
+ *   - Calls are stream-ordered like the context's; a table is for one stream
+ *     (or ordered streams) and one host thread at a time. */
+
+/* The 2k + 1 short-hash keys for a seed (host): n = 2 * width_bytes / 8 + 1.
+ * Errors: HT_ERR_WIDTH, HT_ERR_ARG. */
+int ht_short_hash_keys(uint64_t seed64, int width_bytes, uint64_t *keys_out, size_t n);
+
+/* h(digest) above, on the host (the table computes the same on the device).
+ * Errors: HT_ERR_WIDTH, HT_ERR_ARG. */
+int ht_short_hash(const uint64_t *keys, int width_bytes, const uint64_t *digest, uint64_t *out);
+
+/* Creates an empty table for digests of ctx's width (device memory as
+ * above; ctx must outlive it).  max_entries: 1 .. 2^31.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_table_create(ht_ctx *ctx, uint64_t max_entries, uint64_t seed64, ht_table **out);
+int ht_table_destroy(ht_table *t);
+
+/* Removes every entry (on `stream`).  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_table_clear(ht_table *t, ht_stream_t stream);
+
+/* Entries inserted so far; log2 of the slot count; the keys (2k + 1 words). */
+uint64_t ht_table_entries(const ht_table *t);
+int ht_table_slot_bits(const ht_table *t);
+int ht_table_keys(const ht_table *t, uint64_t *keys_out, size_t n);
+
+/* Inserts count digests (device, count*k words, for example ht_hash_batch's
+ * output) as the next ids.  rep_dev (device, count uint32, or NULL):
+ * rep_dev[i] = the smallest id, earlier insertions included, whose digest
+ * equals digest i.  Errors: HT_ERR_ARG, HT_ERR_BUDGET (the table would
+ * exceed max_entries; nothing is inserted), HT_ERR_CUDA. */
+int ht_table_insert(ht_table *t, const uint64_t *digests_dev, size_t count, uint32_t *rep_dev,
+                    ht_stream_t stream);
+
+/* found_dev[i] (device uint32) = the smallest id whose digest equals query
+ * digest i (device, count*k words), or 0xffffffff.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_table_find(ht_table *t, const uint64_t *digests_dev, size_t count, uint32_t *found_dev,
+                  ht_stream_t stream);
+
+/* Waits for `stream`; HT_ERR_BUDGET if a walk ever found no free slot (not
+ * possible while the table is at most half full), else HT_OK. */
+int ht_table_status(ht_table *t, ht_stream_t stream);
 
 /* ---- hashing without allocation ---------------------------------------------
  * (The paper has no counterpart: this serves deployments, not the method.)

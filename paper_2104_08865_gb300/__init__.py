@@ -10,7 +10,7 @@ import importlib
 
 import numpy as np
 
-__all__ = ["abi", "HalftimeError", "WIDTHS", "Hasher", "Incremental", "digest_words"]
+__all__ = ["abi", "HalftimeError", "WIDTHS", "Hasher", "Incremental", "Table", "digest_words"]
 WIDTHS = (16, 24, 32, 40)
 
 
@@ -172,3 +172,64 @@ class Incremental:
 
     def import_state(self, state: bytes, stream=None):
         _abi().ht_inc_import(self.h, state, self._stream(stream))
+
+
+class Table:
+    """Long strings in a device hash table by their digests (ht_table): insert
+    digests (a CUDA int64 tensor of shape (count, k), e.g. hash_batch's
+    output) to get every entry's representative (the smallest id with an
+    equal digest), find digests to get the id of an equal entry."""
+
+    def __init__(self, hasher: Hasher, max_entries: int, seed64: int = 0x7AB1E):
+        self.hasher = hasher
+        self.k = hasher.k
+        self.t = _abi().ht_table_create(hasher.ctx, max_entries, seed64)
+
+    def close(self):
+        if self.t:
+            _abi().ht_table_destroy(self.t)
+            self.t = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        return stream if stream is not None else torch.cuda.current_stream()
+
+    def insert(self, digests, rep: bool = True, stream=None):
+        """Inserts the rows of `digests`; returns their representatives (a
+        CUDA int32 tensor holding uint32 ids) or None."""
+        import torch
+        count = digests.shape[0]
+        out = torch.empty(count, dtype=torch.int32, device=digests.device) if rep else None
+        _abi().ht_table_insert(self.t, digests, count, out, self._stream(stream))
+        return out
+
+    def find(self, digests, stream=None):
+        """Ids of entries equal to the rows of `digests` (0xffffffff, i.e. -1
+        as int32, where none)."""
+        import torch
+        count = digests.shape[0]
+        out = torch.empty(count, dtype=torch.int32, device=digests.device)
+        _abi().ht_table_find(self.t, digests, count, out, self._stream(stream))
+        return out
+
+    def clear(self, stream=None):
+        _abi().ht_table_clear(self.t, self._stream(stream))
+
+    def entries(self) -> int:
+        return _abi().ht_table_entries(self.t)
+
+    def status(self, stream=None):
+        _abi().ht_table_status(self.t, self._stream(stream))

@@ -94,6 +94,17 @@ _PROTOS = {
     "ht_inc_state_bytes": (_sz, [_vp]),
     "ht_inc_export": (_int, [_vp, _vp, _sz, _vp]),
     "ht_inc_import": (_int, [_vp, _vp, _sz, _vp]),
+    "ht_short_hash_keys": (_int, [_u64, _int, _u64p, _sz]),
+    "ht_short_hash": (_int, [_u64p, _int, _u64p, _u64p]),
+    "ht_table_create": (_int, [_vp, _u64, _u64, ctypes.POINTER(_vp)]),
+    "ht_table_destroy": (_int, [_vp]),
+    "ht_table_clear": (_int, [_vp, _vp]),
+    "ht_table_entries": (_u64, [_vp]),
+    "ht_table_slot_bits": (_int, [_vp]),
+    "ht_table_keys": (_int, [_vp, _u64p, _sz]),
+    "ht_table_insert": (_int, [_vp, _vp, _sz, _vp, _vp]),
+    "ht_table_find": (_int, [_vp, _vp, _sz, _vp, _vp]),
+    "ht_table_status": (_int, [_vp, _vp]),
     "ht_part_granule": (_u64, [_vp]),
     "ht_part_state_words": (_sz, [_vp, _u64]),
     "ht_part_begin": (_int, [_vp, _u64, _vp, _sz, _vp]),
@@ -295,6 +306,61 @@ def ht_inc_export(h: int, stream=None) -> bytes:
 def ht_inc_import(h: int, state: bytes, stream=None) -> None:
     buf = ctypes.create_string_buffer(bytes(state), len(state))
     _check(_lib.ht_inc_import(h, buf, len(state), _stream(stream)))
+
+
+def ht_short_hash_keys(seed64: int, width: int) -> np.ndarray:
+    out = np.zeros(2 * (width // 8) + 1, dtype=np.uint64)
+    _check(_lib.ht_short_hash_keys(seed64, width, out.ctypes.data_as(_u64p), out.size))
+    return out
+
+
+def ht_short_hash(keys, width: int, digest) -> int:
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    digest = np.ascontiguousarray(digest, dtype=np.uint64)
+    out = ctypes.c_uint64()
+    _check(_lib.ht_short_hash(keys.ctypes.data_as(_u64p), width, digest.ctypes.data_as(_u64p),
+                              ctypes.byref(out)))
+    return out.value
+
+
+def ht_table_create(ctx: int, max_entries: int, seed64: int) -> int:
+    t = _vp()
+    _check(_lib.ht_table_create(ctx, max_entries, seed64, ctypes.byref(t)))
+    return t.value
+
+
+def ht_table_destroy(t: int) -> None:
+    _check(_lib.ht_table_destroy(t))
+
+
+def ht_table_clear(t: int, stream=None) -> None:
+    _check(_lib.ht_table_clear(t, _stream(stream)))
+
+
+def ht_table_entries(t: int) -> int:
+    return int(_lib.ht_table_entries(t))
+
+
+def ht_table_slot_bits(t: int) -> int:
+    return int(_lib.ht_table_slot_bits(t))
+
+
+def ht_table_keys(t: int, width: int) -> np.ndarray:
+    out = np.zeros(2 * (width // 8) + 1, dtype=np.uint64)
+    _check(_lib.ht_table_keys(t, out.ctypes.data_as(_u64p), out.size))
+    return out
+
+
+def ht_table_insert(t: int, digests_dev, count: int, rep_dev=None, stream=None) -> None:
+    _check(_lib.ht_table_insert(t, _ptr(digests_dev), count, _ptr(rep_dev), _stream(stream)))
+
+
+def ht_table_find(t: int, digests_dev, count: int, found_dev, stream=None) -> None:
+    _check(_lib.ht_table_find(t, _ptr(digests_dev), count, _ptr(found_dev), _stream(stream)))
+
+
+def ht_table_status(t: int, stream=None) -> None:
+    _check(_lib.ht_table_status(t, _stream(stream)))
 
 
 def ht_part_granule(ctx: int) -> int:

@@ -54,7 +54,7 @@ const KernelSet *kernel_set(int width) {
 
 // ---- seeds: splitmix64 (Steele, Lea, Flood 2014) ------------------------------
 
-static uint64_t splitmix64_next(uint64_t *state) {
+uint64_t splitmix64_next(uint64_t *state) {
   uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;

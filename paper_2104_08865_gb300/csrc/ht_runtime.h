@@ -63,6 +63,8 @@ int cuda_error(cudaError_t e, const char *what);
 const KernelSet *kernel_set(int width);
 uint64_t items_of(uint64_t N, int L);
 uint64_t groups_of(uint64_t N, int L);
+// The next output of splitmix64 (Steele, Lea and Flood 2014) from *state.
+uint64_t splitmix64_next(uint64_t *state);
 // Zeroes P, then fills the hash keys, the seed pointer and the context's scratch.
 void fill_keys(const ht_ctx *c, KParams &P);
 }  // namespace ht
