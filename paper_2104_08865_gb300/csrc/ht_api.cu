@@ -100,6 +100,11 @@ static void free_scratch(ht_ctx *c) {
   cudaFree(c->item0s);
   cudaFree(c->chunk0s);
   cudaFree(c->unitb0s);
+  cudaFree(c->tile_items);
+  cudaFree(c->tile_groups);
+  cudaFree(c->tile_flags);
+  c->tile_items = c->tile_groups = nullptr;
+  c->tile_flags = nullptr;
   c->chunk0s = nullptr;
   c->unitb0s = nullptr;
   c->grp_acc = nullptr;
@@ -129,6 +134,10 @@ static int alloc_scratch(ht_ctx *c, uint64_t groups, uint64_t strings) {
   grab((void **)&c->item0s, (strings + 1) * sizeof(unsigned long long));
   grab((void **)&c->chunk0s, (strings + 1) * sizeof(unsigned long long));
   grab((void **)&c->unitb0s, (strings + 1) * sizeof(unsigned long long));
+  const uint64_t tiles = (strings + 1023) / 1024 + 1;
+  grab((void **)&c->tile_items, tiles * sizeof(unsigned long long));
+  grab((void **)&c->tile_groups, tiles * sizeof(unsigned long long));
+  grab((void **)&c->tile_flags, tiles * sizeof(unsigned int));
   if (e != cudaSuccess) {
     free_scratch(c);
     return cuda_error(e, "scratch allocation");
@@ -506,18 +515,48 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
   return HT_OK;
 }
 
-// The batch graph: planner node -> hash node.  Node parameters are replaced
-// on every call; the graph is rebuilt when the batch shape changes.
-static void batch_nodes(ht_ctx *c, const ht_shape &shape, cudaKernelNodeParams &np,
-                        cudaKernelNodeParams &nh, void **pargs, void **hargs) {
+// The batch graph: planner nodes -> hash node(s).  The warp-chunk and
+// stream kernels take the multi-block planner (tiles -> totals -> write, one
+// thread per string); the hybrid kernel takes the one-block planner, which
+// also lays out its two-phase work list.  Node parameters are replaced on
+// every call; the graph is rebuilt when the batch shape changes.
+struct BatchNodes {
+  cudaKernelNodeParams plan, totals, write, hash, hash2;
+  void *pargs[1], *hargs[1];
+  bool multi;   // multi-block planner
+  bool general; // a general (unaligned-capable) batch kernel follows the aligned-only one
+};
+
+// The general (unaligned-capable) batch kernel paired with the aligned-only
+// one of a shape (none for the stream kernel, which handles both).
+static const void *general_batch_kernel(const ht_ctx *c, const ht_shape &shape) {
+  return shape.kernel == 2 ? c->ks->range_batch_unaligned : c->ks->batch_unaligned[shape.chunk_levels - 1];
+}
+
+static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
   const KernelSet &ks = *c->ks;
-  np = {};
-  np.func = (void *)ks.plan[shape.kernel != 1 ? 0 : shape.chunk_levels];
-  np.gridDim = dim3(1);
-  np.blockDim = dim3(1024);
-  pargs[0] = &c->plan_args;
-  np.kernelParams = pargs;
-  nh = {};
+  const int pl = shape.kernel == 1 ? shape.chunk_levels : 0;
+  n.multi = shape.kernel != 2;
+  n.general = shape.kernel != 0;
+  n.pargs[0] = &c->plan_args;
+  const unsigned tiles = std::max(1u, (c->plan_args.count + 1023) / 1024);
+  c->plan_args.n_tiles = tiles;
+  n.plan = {};
+  n.plan.blockDim = dim3(1024);
+  n.plan.kernelParams = n.pargs;
+  if (n.multi) {
+    n.plan.func = (void *)ks.plan_tiles[pl];
+    n.plan.gridDim = dim3(tiles);
+    n.totals = n.plan;
+    n.totals.func = (void *)ks.plan_totals;
+    n.totals.gridDim = dim3(1);
+    n.write = n.plan;
+    n.write.func = (void *)ks.plan_write[pl];
+  } else {
+    n.plan.func = (void *)ks.plan[pl];
+    n.plan.gridDim = dim3(1);
+  }
+  n.hash = {};
   size_t smem = 0;
   const void *func;
   if (shape.kernel == 0) {
@@ -530,21 +569,17 @@ static void batch_nodes(ht_ctx *c, const ht_shape &shape, cudaKernelNodeParams &
   }
   const int tpb = shape.threads_per_block;
   const int bps = std::max(1, std::min(shape.blocks_per_sm, occupancy(func, tpb, smem)));
-  nh.func = (void *)func;
-  nh.gridDim = dim3((unsigned)(c->num_sms * bps));
-  nh.blockDim = dim3(tpb);
-  nh.sharedMemBytes = (unsigned)smem;
+  n.hash.func = (void *)func;
+  n.hash.gridDim = dim3((unsigned)(c->num_sms * bps));
+  n.hash.blockDim = dim3(tpb);
+  n.hash.sharedMemBytes = (unsigned)smem;
   c->batch_params.total_warps = (unsigned)(c->num_sms * bps * (tpb / 32));
   c->batch_params.stages = (unsigned)shape.stages;
   c->plan_args.total_warps = c->batch_params.total_warps;
-  hargs[0] = &c->batch_params;
-  nh.kernelParams = hargs;
-}
-
-// The general (unaligned-capable) batch kernel paired with the aligned-only
-// one of a shape (none for the stream kernel, which handles both).
-static const void *general_batch_kernel(const ht_ctx *c, const ht_shape &shape) {
-  return shape.kernel == 2 ? c->ks->range_batch_unaligned : c->ks->batch_unaligned[shape.chunk_levels - 1];
+  n.hargs[0] = &c->batch_params;
+  n.hash.kernelParams = n.hargs;
+  n.hash2 = n.hash;
+  if (n.general) n.hash2.func = (void *)general_batch_kernel(c, shape);
 }
 
 static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
@@ -552,19 +587,23 @@ static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
   c->graph = nullptr;
-  c->node_hash2 = nullptr;
-  cudaKernelNodeParams np, nh;
-  void *pargs[1], *hargs[1];
-  batch_nodes(c, shape, np, nh, pargs, hargs);
+  c->node_hash2 = c->node_totals = c->node_write = nullptr;
+  BatchNodes n;
+  batch_nodes(c, shape, n);
   HT_CUDA(cudaGraphCreate(&c->graph, 0));
-  HT_CUDA(cudaGraphAddKernelNode(&c->node_plan, c->graph, nullptr, 0, &np));
-  HT_CUDA(cudaGraphAddKernelNode(&c->node_hash, c->graph, &c->node_plan, 1, &nh));
-  if (shape.kernel != 0) {
-    // the general (unaligned-capable) variant; the one the planner's flag
-    // does not select returns at once
-    cudaKernelNodeParams nu = nh;
-    nu.func = (void *)general_batch_kernel(c, shape);
-    HT_CUDA(cudaGraphAddKernelNode(&c->node_hash2, c->graph, &c->node_hash, 1, &nu));
+  HT_CUDA(cudaGraphAddKernelNode(&c->node_plan, c->graph, nullptr, 0, &n.plan));
+  cudaGraphNode_t last = c->node_plan;
+  if (n.multi) {
+    HT_CUDA(cudaGraphAddKernelNode(&c->node_totals, c->graph, &last, 1, &n.totals));
+    last = c->node_totals;
+    HT_CUDA(cudaGraphAddKernelNode(&c->node_write, c->graph, &last, 1, &n.write));
+    last = c->node_write;
+  }
+  HT_CUDA(cudaGraphAddKernelNode(&c->node_hash, c->graph, &last, 1, &n.hash));
+  if (n.general) {
+    // the general variant; the one the planner's flag does not select
+    // returns at once
+    HT_CUDA(cudaGraphAddKernelNode(&c->node_hash2, c->graph, &c->node_hash, 1, &n.hash2));
   }
   HT_CUDA(cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
   c->graph_shape = shape;
@@ -592,6 +631,9 @@ int ht_hash_batch(ht_ctx *c, const void *const *ptrs, const uint64_t *lens, size
   A.unitb0s = c->unitb0s;
   A.ctl = c->ctl;
   A.cap_groups = c->cap_groups;
+  A.tile_items = c->tile_items;
+  A.tile_groups = c->tile_groups;
+  A.tile_flags = c->tile_flags;
   KParams &P = c->batch_params;
   fill_keys(c, P);
   P.plans = c->plans;
@@ -604,19 +646,16 @@ int ht_hash_batch(ht_ctx *c, const void *const *ptrs, const uint64_t *lens, size
     int rc = build_batch_graph(c, shape);
     if (rc) return rc;
   } else {
-    cudaKernelNodeParams np, nh;
-    void *pargs[1], *hargs[1];
-    batch_nodes(c, shape, np, nh, pargs, hargs);
-    HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_plan, &np));
-    HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash, &nh));
-    if (c->node_hash2) {
-      cudaKernelNodeParams nu = nh;
-      nu.func = (void *)general_batch_kernel(c, shape);
-      HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash2, &nu));
-    }
+    BatchNodes n;
+    batch_nodes(c, shape, n);
+    HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_plan, &n.plan));
+    if (c->node_totals) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_totals, &n.totals));
+    if (c->node_write) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_write, &n.write));
+    HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash, &n.hash));
+    if (c->node_hash2) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash2, &n.hash2));
   }
   HT_CUDA(cudaGraphLaunch(c->graph_exec, s));
-  c->launches.fetch_add(c->node_hash2 ? 3 : 2);
+  c->launches.fetch_add(2 + (c->node_totals ? 2 : 0) + (c->node_hash2 ? 1 : 0));
   return HT_OK;
 }
 

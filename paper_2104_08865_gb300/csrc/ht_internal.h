@@ -87,6 +87,12 @@ struct PlanArgs {
   Ctl *ctl;
   uint64_t cap_groups;
   unsigned int total_warps;  // warps of the hash kernel (hybrid work list)
+  // multi-block planner: per tile of 1024 strings, its item and group totals
+  // (then their exclusive prefix sums) and whether it holds an unaligned string
+  unsigned long long *tile_items;
+  unsigned long long *tile_groups;
+  unsigned int *tile_flags;
+  unsigned int n_tiles;
 };
 
 // Kernel variants of one width.  Warp-chunk kernels: chunk height L in
@@ -98,7 +104,10 @@ struct KernelSet {
   const void *single_unaligned[3];  // [L-1]
   const void *batch[3];             // [L-1], aligned-only
   const void *batch_unaligned[3];   // [L-1], general (see ctl.unaligned)
-  const void *plan[4];              // [0]: stream, [L]: warp-chunk
+  const void *plan[4];              // [0]: stream, [L]: warp-chunk (one block, hybrid work list too)
+  const void *plan_tiles[4];        // multi-block planner, same index: tile totals
+  const void *plan_totals;          //   their prefix sums and the batch totals
+  const void *plan_write[4];        //   every string's plan
   const void *stream_single;
   const void *stream_batch;
   const void *range_single;  // hybrid kernel: chunks then units from a cursor

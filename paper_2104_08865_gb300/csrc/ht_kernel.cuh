@@ -223,18 +223,16 @@ __device__ __forceinline__ uint64_t final_key(const KParams &P, int t, int lvl, 
 
 // ---- the finaliser: pending-root sum + Toeplitz tail (Section 6.1) ----------
 
+// The Toeplitz tail NH of the string, length word included (Section 6.1, and
+// reading 9), summed over the warp: every lane gets the k sums.
 template <int W>
-__device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx, int ln) {
+__device__ __forceinline__ void tail_sum(const KParams &P, const StrPlan &sp, int ln,
+                                         uint64_t (&sum)[Spec<W>::k]) {
   constexpr int k = Spec<W>::k;
   constexpr int B = Dims<W>::exec_bytes;
-  __threadfence();
-  uint64_t acc[k];
-#pragma unroll
-  for (int t = 0; t < k; ++t) acc[t] = ld_cg(P.scr.str_acc + (uint64_t)sidx * k + t);
   const uint64_t tstart = sp.n_exec * (uint64_t)B;
   const uint64_t tlen = sp.len - tstart;  // < B
   const uint32_t M = (uint32_t)((tlen + 7) / 8);
-  uint64_t sum[k];
 #pragma unroll
   for (int t = 0; t < k; ++t) sum[t] = 0;
   for (uint32_t m = ln; m <= M; m += 32) {
@@ -250,6 +248,17 @@ __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx
   }
 #pragma unroll
   for (int t = 0; t < k; ++t) sum[t] = warp_sum(sum[t]);
+}
+
+template <int W>
+__device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx, int ln) {
+  constexpr int k = Spec<W>::k;
+  __threadfence();
+  uint64_t acc[k];
+#pragma unroll
+  for (int t = 0; t < k; ++t) acc[t] = ld_cg(P.scr.str_acc + (uint64_t)sidx * k + t);
+  uint64_t sum[k];
+  tail_sum<W>(P, sp, ln, sum);
   if (ln == 0) {
 #pragma unroll
     for (int t = 0; t < k; ++t) {
@@ -258,6 +267,22 @@ __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx
     }
     P.scr.str_done[sidx] = 0;
   }
+}
+
+// A string with a single work item: its warp holds the whole final-NH sum
+// (pend, spread over the lanes), so it writes the digest without the
+// string's scratch sum and completion count.
+template <int W>
+__device__ void finish_local(const KParams &P, const StrPlan &sp, unsigned sidx,
+                             uint64_t (&pend)[Spec<W>::k], int ln) {
+  constexpr int k = Spec<W>::k;
+  uint64_t sum[k];
+  tail_sum<W>(P, sp, ln, sum);
+#pragma unroll
+  for (int t = 0; t < k; ++t) sum[t] += warp_sum(pend[t]);
+  if (ln == 0)
+#pragma unroll
+    for (int t = 0; t < k; ++t) P.digests[(uint64_t)sidx * k + t] = sum[t];
 }
 
 // ---- one work item: a chunk of 8^L executions ---------------------------------
@@ -541,6 +566,11 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, u
   const bool full = chunk_root<W, L, ALIGNED>(P, sp, sp.ptr, c, ln, pend, anyp, v0, v1);
   griddep_wait();
   if (full) climb<W, false>(P, sp, L, c, 0, v0, v1, ln, pend, anyp);
+  if (sp.n_items == 1) {
+    // (a single chunk's root is a pending root: the climb touched no scratch)
+    finish_local<W>(P, sp, sidx, pend, ln);
+    return;
+  }
   flush_pending<W>(P, sidx, pend, anyp, ln);
   __threadfence();
   __syncwarp();
@@ -661,6 +691,26 @@ __device__ __forceinline__ unsigned find_string(const unsigned long long *item0s
   return lo;
 }
 
+// The same search by a whole (converged) warp: every step probes 32 evenly
+// spaced entries of (lo, hi] at once, lane j at lo + span (j + 1) / 32 (lane
+// 31 at hi, known to be > item, and not loaded), and keeps the interval
+// between the last probe <= item and the first one > item: about 32 times
+// smaller, so 50,000 strings take 4 dependent loads instead of 16.
+__device__ __forceinline__ unsigned find_string_warp(const unsigned long long *item0s,
+                                                     unsigned count, uint64_t item, int ln) {
+  unsigned lo = 0, hi = count;  // item0s[lo] <= item < item0s[hi]
+  while (hi - lo > 1) {
+    const uint64_t span = hi - lo;
+    const unsigned pos = lo + (unsigned)((span * (unsigned)(ln + 1)) >> 5);
+    const bool le = pos < hi && __ldg(item0s + pos) <= item;
+    const unsigned j = (unsigned)__popc(__ballot_sync(kFull, le));  // probes 0 .. j-1 are <= item
+    const unsigned nlo = lo + (unsigned)((span * j) >> 5);
+    hi = lo + (unsigned)((span * (j + 1)) >> 5);
+    lo = nlo;
+  }
+  return lo;
+}
+
 // Every warp passes here on leaving; the last one (all other warps' work is
 // then visible to it) rearms the cursor for the next launch and learns that
 // it was last.
@@ -707,7 +757,7 @@ __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KP
       if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
       item = __shfl_sync(kFull, item, 0);
       if (item >= total) break;
-      const unsigned s = find_string(P.item0s, P.count, item);
+      const unsigned s = find_string_warp(P.item0s, P.count, item, ln);
       const StrPlan sp = P.plans[s];
       const uint64_t c = item - sp.item0;
       if (ALIGNED || (((uintptr_t)sp.ptr) & 15u) == 0)
@@ -842,6 +892,117 @@ __global__ void __launch_bounds__(1024) plan_kernel(const PlanArgs A) {
     A.ctl->units_b = total_b;
     A.ctl->unaligned = any_unaligned ? 1u : 0u;
     if (total_g > A.cap_groups) A.ctl->status = kStatusTooLong;
+  }
+}
+
+// The multi-block batch planner (warp-chunk and stream kernels), three
+// launches over tiles of 1024 strings, one thread per string and coalesced
+// loads: it computes the plans that the one-block planner above computes,
+// less the hybrid kernel's work list.
+
+template <int L>
+__device__ __forceinline__ unsigned long long plan_items(uint64_t N) {
+  if (L == 0) return ((N + 7) >> 3) + 1;
+  const uint64_t it = (N + (1ull << (3 * L)) - 1) >> (3 * L);
+  return it ? it : 1ull;
+}
+template <int L>
+__device__ __forceinline__ unsigned long long plan_groups(uint64_t N) {
+  uint64_t g = 0;
+  for (int lvl = (L == 0 ? 1 : L); lvl < kLevels; ++lvl) g += N >> (3 * lvl + 3);
+  return g;
+}
+
+// 1: the work items and tree-group slots of every string of a tile, the
+// tile's totals and whether it holds a string that is not 16-byte aligned.
+template <int W, int L>
+__global__ void __launch_bounds__(1024) plan_tiles_kernel(const PlanArgs A) {
+  constexpr uint64_t B = Dims<W>::exec_bytes;
+  __shared__ unsigned long long sh[32];
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long it = 0, gr = 0;
+  bool un = false;
+  if (i < A.count) {
+    const uint64_t N = A.lens[i] / B;
+    it = plan_items<L>(N);
+    gr = plan_groups<L>(N);
+    un = (((uintptr_t)A.ptrs[i]) & 15u) != 0;
+  }
+  const int any_un = __syncthreads_or(un);
+  unsigned long long ti, tg;
+  block_scan(it, sh, &ti);
+  block_scan(gr, sh, &tg);
+  if (threadIdx.x == 0) {
+    A.tile_items[blockIdx.x] = ti;
+    A.tile_groups[blockIdx.x] = tg;
+    A.tile_flags[blockIdx.x] = any_un ? 1u : 0u;
+  }
+}
+
+// 2 (one block): the tiles' exclusive prefix sums, in place, the batch's
+// totals, the capacity check and the alignment flag.
+template <int W>
+__global__ void __launch_bounds__(1024) plan_totals_kernel(const PlanArgs A) {
+  __shared__ unsigned long long sh[32];
+  unsigned long long base_i = 0, base_g = 0;
+  int any_un = 0;
+  for (unsigned t0 = 0; t0 < A.n_tiles; t0 += blockDim.x) {
+    const unsigned t = t0 + threadIdx.x;
+    const bool in = t < A.n_tiles;
+    const unsigned long long vi = in ? A.tile_items[t] : 0, vg = in ? A.tile_groups[t] : 0;
+    any_un |= __syncthreads_or(in && A.tile_flags[t] != 0);
+    unsigned long long ti, tg;
+    const unsigned long long ei = block_scan(vi, sh, &ti);
+    const unsigned long long eg = block_scan(vg, sh, &tg);
+    if (in) {
+      A.tile_items[t] = base_i + ei;
+      A.tile_groups[t] = base_g + eg;
+    }
+    base_i += ti;
+    base_g += tg;
+  }
+  if (threadIdx.x == 0) {
+    A.item0s[A.count] = base_i;
+    A.ctl->total = base_i;
+    A.ctl->groups = base_g;
+    A.ctl->chunks_a = 0;
+    A.ctl->units_b = 0;
+    A.ctl->unaligned = any_un ? 1u : 0u;
+    if (base_g > A.cap_groups) A.ctl->status = kStatusTooLong;
+  }
+}
+
+// 3: every string's plan, its first item and its first group slot.
+template <int W, int L>
+__global__ void __launch_bounds__(1024) plan_write_kernel(const PlanArgs A) {
+  constexpr uint64_t B = Dims<W>::exec_bytes;
+  __shared__ unsigned long long sh[32];
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t len = 0, N = 0;
+  unsigned long long it = 0, gr = 0;
+  if (i < A.count) {
+    len = A.lens[i];
+    N = len / B;
+    it = plan_items<L>(N);
+    gr = plan_groups<L>(N);
+  }
+  unsigned long long ti, tg;
+  const unsigned long long ei = block_scan(it, sh, &ti) + A.tile_items[blockIdx.x];
+  const unsigned long long eg = block_scan(gr, sh, &tg) + A.tile_groups[blockIdx.x];
+  if (i < A.count) {
+    StrPlan sp;
+    sp.ptr = static_cast<const uint8_t *>(A.ptrs[i]);
+    sp.len = len;
+    sp.n_exec = N;
+    sp.item0 = ei;
+    sp.grp0 = eg;
+    sp.n_items = (uint32_t)it;
+    sp.pad = 0;
+    sp.chunk0 = 0;
+    sp.chunks_a = 0;
+    sp.unitb0 = 0;
+    A.plans[i] = sp;
+    A.item0s[i] = ei;
   }
 }
 

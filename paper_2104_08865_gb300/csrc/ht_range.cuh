@@ -255,6 +255,15 @@ KernelSet make_kernel_set() {
   ks.plan[1] = (const void *)plan_kernel<W, 1>;
   ks.plan[2] = (const void *)plan_kernel<W, 2>;
   ks.plan[3] = (const void *)plan_kernel<W, 3>;
+  ks.plan_tiles[0] = (const void *)plan_tiles_kernel<W, 0>;
+  ks.plan_tiles[1] = (const void *)plan_tiles_kernel<W, 1>;
+  ks.plan_tiles[2] = (const void *)plan_tiles_kernel<W, 2>;
+  ks.plan_tiles[3] = (const void *)plan_tiles_kernel<W, 3>;
+  ks.plan_totals = (const void *)plan_totals_kernel<W>;
+  ks.plan_write[0] = (const void *)plan_write_kernel<W, 0>;
+  ks.plan_write[1] = (const void *)plan_write_kernel<W, 1>;
+  ks.plan_write[2] = (const void *)plan_write_kernel<W, 2>;
+  ks.plan_write[3] = (const void *)plan_write_kernel<W, 3>;
   ks.stream_single = (const void *)stream_kernel<W, false>;
   ks.stream_batch = (const void *)stream_kernel<W, true>;
   ks.range_single = (const void *)range_kernel<W, false, true>;

@@ -31,6 +31,9 @@ struct ht_ctx {
   unsigned long long *item0s = nullptr;
   unsigned long long *chunk0s = nullptr;
   unsigned long long *unitb0s = nullptr;
+  unsigned long long *tile_items = nullptr;   // multi-block planner, per 1024 strings
+  unsigned long long *tile_groups = nullptr;
+  unsigned int *tile_flags = nullptr;
   ht::Ctl *ctl = nullptr;
   uint64_t cap_groups = 0, cap_strings = 0;
   // launch shapes: [0..63] by floor(log2(len)), [64] batches
@@ -39,6 +42,7 @@ struct ht_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   cudaGraphNode_t node_plan = nullptr, node_hash = nullptr, node_hash2 = nullptr;
+  cudaGraphNode_t node_totals = nullptr, node_write = nullptr;  // multi-block planner (else null)
   ht_shape graph_shape = {};
   bool graph_valid = false;
   ht::PlanArgs plan_args = {};

@@ -210,9 +210,10 @@ def test_launch_counter_counts_kernels(dev):
     torch.cuda.synchronize()
     from paper_2104_08865_gb300 import abi
     batch_kernel = abi.ht_get_shape(h.ctx, 2**64 - 1)["kernel"]
-    # one hash kernel, then the planner and the batch kernels (an aligned
-    # and a general one, except for the stream family)
-    assert h.launches() - before == 1 + (2 if batch_kernel == 0 else 3)
+    # one hash kernel, then the planner (three launches, one for the hybrid
+    # family) and the batch kernels (an aligned and a general one, except for
+    # the stream family)
+    assert h.launches() - before == 1 + {0: 4, 1: 5, 2: 3}[batch_kernel]
 
 
 @pytest.mark.parametrize("width", WIDTHS)
