@@ -186,6 +186,23 @@ def test_c4_batch_50000_log_uniform(dev, shape):
     assert np.array_equal(got, want)
 
 
+def test_batch_of_a_million_short_strings(dev):
+    """1,050,000 strings of 0 .. 1400 bytes (tail-only, or one execution and
+    a tail), width 16: 1026 planner tiles, more than the 1024 that one pass
+    of the totals kernel scans; every digest against the oracle."""
+    from paper_2104_08865_gb300 import abi
+    width = 16
+    h, ref = _pair(width)
+    rng = np.random.default_rng(77)
+    lens = rng.integers(0, 1401, size=1_050_000).astype(np.int64)
+    buf, offs = inputs.packed_batch(5, lens)
+    abi.ht_ctx_reserve(h.ctx, int(buf.size), len(lens))
+    dbuf = torch.from_numpy(buf).to(dev)
+    got = _batch(h, dbuf, offs, lens)
+    h.status()
+    assert np.array_equal(got, oracle.hash_many(width, ref, buf, offs, lens))
+
+
 @pytest.mark.parametrize("width", [24, 40])
 def test_autotuned_shape_keeps_digests(dev, width):
     from paper_2104_08865_gb300 import abi
