@@ -140,10 +140,12 @@ int ht_hash_host(ht_ctx *ctx, const void *data_host, uint64_t len,
 /* Hashes `count` device-resident strings in one persistent launch (the batch
  * form): ptrs_dev[i] / lens_dev[i] (device arrays) describe string i, and
  * digests_dev receives count*k words, string i at digests_dev + i*k.  A
- * device planner turns the lengths into a (string, chunk) work list; warps
- * take chunks from an atomic cursor; per-string completion counters finish
- * each string's trees and run its finaliser inside the same kernel.  The
- * planner and the kernel are replayed from a CUDA graph.  The batch must fit
+ * device planner (three launches over tiles of 1024 strings) turns the
+ * lengths into a (string, chunk) work list; warps take chunks from an
+ * atomic cursor; per-string completion counters finish each string's trees
+ * and run its finaliser inside the same kernel (a string shorter than one
+ * chunk is finished by the warp that hashes it).  The planner and the
+ * kernel are replayed from a CUDA graph.  The batch must fit
  * the scratch reserved by ht_ctx_reserve: the planner checks this on the
  * device and, if it does not fit, writes no digests and records
  * HT_ERR_TOO_LONG for ht_ctx_status (the host cannot see device lengths).
