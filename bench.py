@@ -427,21 +427,28 @@ def run_serving(args, dev, stream):
     h = Hasher(32, seed_words=abi.ht_seed_expand(SEED_KEY, 32))
     mean_len = None
     out = {"workload": "width 32, lengths log-uniform 256 B..64 MiB, Poisson arrivals, budget 16 GiB, "
-                       "%.1f s per load point" % args.serve_seconds, "forms": {}}
+                       "%.1f s per load point" % args.serve_seconds, "forms": {},
+           "form_notes": {"device": "requests already in device memory",
+                          "pinned_h2d": "pinned host requests read in place by the batch kernel over "
+                                        "the CPU-GPU link (the server's default)",
+                          "pinned_h2d_staged": "pinned host requests copied into a device arena first"}}
 
     def requests(n, seed):
         ln = inputs.log_uniform_lengths(seed, n, 256, 64 << 20)
         off = (rng.integers(0, pool_bytes - (64 << 20), n) // 256) * 256
         return ln, off
 
-    for form, base, pinned in (("device", pool_dev.data_ptr(), 0),
-                               ("pinned_h2d", pool_host.data_ptr(), 1)):
+    # pinned host requests: read in place by the batch kernel over the
+    # CPU-GPU link (the server's default), and staged through device memory
+    for form, base, pinned, mode in (("device", pool_dev.data_ptr(), 0, 0),
+                                     ("pinned_h2d", pool_host.data_ptr(), 1, 0),
+                                     ("pinned_h2d_staged", pool_host.data_ptr(), 1, 1)):
         res = {}
         # peak: bursts with every request arriving at once, sized to tens of
         # milliseconds of work; the better of two
         nburst = 10000 if form == "device" else 2000
         ln, off = requests(nburst, 61)
-        srv = abi.ht_server_create(h.ctx, 16 << 30, n_streams=4, max_batch=4096)
+        srv = abi.ht_server_create(h.ctx, 16 << 30, n_streams=4, max_batch=4096, pinned_mode=mode)
         dig = np.zeros((nburst, 4), dtype=np.uint64)
         peak = 0.0
         for _ in range(2):

@@ -428,6 +428,10 @@ typedef struct ht_server_opts {
   size_t max_batch;       /* requests per batch (default 4096) */
   size_t max_queue;       /* queued requests before submit says BUSY (default 1<<20) */
   uint64_t max_wait_us;   /* longest a request waits for batch-mates (default 0) */
+  int pinned_mode;        /* pinned-host requests: 0 (default) = read in place by the
+                             batch kernel when the GPU can address the memory (on
+                             GB300 the coherent CPU-GPU link), else staged; 1 = always
+                             staged, copied into a device arena first */
 } ht_server_opts;
 
 typedef struct ht_server_stats_t {

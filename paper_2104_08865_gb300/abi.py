@@ -48,7 +48,8 @@ class ht_shape(ctypes.Structure):
 
 class ht_server_opts(ctypes.Structure):
     _fields_ = [("n_streams", ctypes.c_int), ("max_batch", ctypes.c_size_t),
-                ("max_queue", ctypes.c_size_t), ("max_wait_us", ctypes.c_uint64)]
+                ("max_queue", ctypes.c_size_t), ("max_wait_us", ctypes.c_uint64),
+                ("pinned_mode", ctypes.c_int)]
 
 
 class ht_server_stats_t(ctypes.Structure):
@@ -417,8 +418,8 @@ def ht_ctx_launches(ctx: int) -> int:
     return int(_lib.ht_ctx_launches(ctx))
 
 
-def _opts(n_streams=0, max_batch=0, max_queue=0, max_wait_us=0):
-    return ht_server_opts(n_streams, max_batch, max_queue, max_wait_us)
+def _opts(n_streams=0, max_batch=0, max_queue=0, max_wait_us=0, pinned_mode=0):
+    return ht_server_opts(n_streams, max_batch, max_queue, max_wait_us, pinned_mode)
 
 
 def ht_server_create(ctx: int, budget_bytes: int, **opts) -> int:

@@ -2,8 +2,11 @@
 //
 // Requests arrive on any thread (ht_server_submit).  A dispatcher thread turns
 // the head of the FIFO queue into a batch as soon as a stream slot is free,
-// admitting requests while their bytes fit the memory budget; pinned-host
-// requests are staged into a device arena carved from that budget.  Each slot
+// admitting requests while their bytes fit the memory budget.  Pinned-host
+// requests that the GPU can address are read in place by the batch kernel
+// (on GB300 over the coherent CPU-GPU link: no copy call per request, no
+// arena space); others, or all with pinned_mode 1, are staged into a device
+// arena carved from that budget.  Each slot
 // owns its own context (so its tree scratch never races another slot's), its
 // stream and pinned descriptor buffers; a batch is one ht_hash_batch (planner
 // + persistent kernel replayed from a graph) followed by a digest copy and an
@@ -47,6 +50,7 @@ struct Req {
   int status = HT_OK;
   uint64_t arena_off = 0;
   bool has_arena = false;
+  const void *dev_ptr = nullptr;  // pinned request read in place: its device address
 };
 
 // First-fit allocator over [0, size) with 256-byte granules.
@@ -143,7 +147,9 @@ int launch_real(ht_server *S, Slot &sl, const std::vector<Req *> &batch) {
   const size_t n = batch.size();
   for (size_t i = 0; i < n; ++i) {
     Req *r = batch[i];
-    if (r->pinned && r->len) {
+    if (r->dev_ptr) {
+      sl.h_ptrs[i] = r->dev_ptr;  // read in place over the CPU-GPU link
+    } else if (r->pinned && r->len) {
       uint8_t *dst = S->arena_base + r->arena_off;
       cudaError_t e = cudaMemcpyAsync(dst, r->ptr, r->len, cudaMemcpyHostToDevice, sl.stream);
       if (e != cudaSuccess) return ht::cuda_error(e, "request staging copy");
@@ -177,6 +183,20 @@ int poll_slot(ht_server *S, Slot &sl) {
   if (e == cudaErrorNotReady) return 0;
   if (e != cudaSuccess) return ht::cuda_error(e, "batch event");
   return 1;
+}
+
+// The device address of a pinned request that the batch kernel can read in
+// place (pinned host memory the GPU addresses directly), or null: then the
+// request is staged through the arena.
+const void *in_place_address(const ht_server *S, const void *ptr, uint64_t len, int pinned) {
+  if (!pinned || !len || S->fake || S->opts.pinned_mode != 0) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();  // (clears the error: not a device-visible allocation)
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return a.devicePointer;
 }
 
 void release_req(ht_server *S, Req &r) {
@@ -221,7 +241,7 @@ void dispatcher_main(ht_server *S) {
     while (!S->queue.empty() && batch.size() < S->opts.max_batch) {
       Req &r = S->reqs[S->queue.front()];
       if (S->in_use + r.len > S->budget) break;
-      if (r.pinned && r.len) {
+      if (r.pinned && r.len && !r.dev_ptr) {
         if (!S->arena.alloc(r.len, &r.arena_off)) break;
         r.has_arena = true;
       }
@@ -334,11 +354,13 @@ int make_server(ht_server *S, ht_ctx *ctx, uint64_t budget, const ht_server_opts
   o.max_batch = 4096;
   o.max_queue = 1u << 20;
   o.max_wait_us = 0;
+  o.pinned_mode = 0;
   if (opts) {
     if (opts->n_streams > 0) o.n_streams = opts->n_streams;
     if (opts->max_batch > 0) o.max_batch = opts->max_batch;
     if (opts->max_queue > 0) o.max_queue = opts->max_queue;
     o.max_wait_us = opts->max_wait_us;
+    o.pinned_mode = opts->pinned_mode;
   }
   S->opts = o;
   S->slots.resize((size_t)o.n_streams);
@@ -455,6 +477,7 @@ int ht_server_submit(ht_server *S, const void *ptr, uint64_t len, int pinned, ui
     return ht::set_error(HT_ERR_BUDGET, "request of %llu bytes exceeds the budget of %llu",
                          (unsigned long long)len, (unsigned long long)S->budget);
   }
+  const void *dev = in_place_address(S, ptr, len, pinned);
   std::lock_guard<std::mutex> g(S->mu);
   if (S->queue.size() >= S->opts.max_queue) {
     S->rejected++;
@@ -464,6 +487,7 @@ int ht_server_submit(ht_server *S, const void *ptr, uint64_t len, int pinned, ui
   r.ptr = ptr;
   r.len = len;
   r.pinned = pinned ? 1 : 0;
+  r.dev_ptr = dev;
   r.digest_host = digest_host;
   r.t_arrive = now_ns();
   S->reqs.push_back(r);
@@ -517,6 +541,8 @@ int ht_server_replay(ht_server *S, const void *const *ptrs, const uint64_t *lens
     if (lens[i] > S->budget)
       return ht::set_error(HT_ERR_BUDGET, "request %zu of %llu bytes exceeds the budget", i,
                            (unsigned long long)lens[i]);
+  std::vector<const void *> dev(n, nullptr);  // in-place addresses, resolved before the clock starts
+  for (size_t i = 0; i < n; ++i) dev[i] = in_place_address(S, ptrs[i], lens[i], pinned ? pinned[i] : 0);
   const size_t first = S->reqs.size();  // tickets are consecutive from here
   const int64_t t0 = now_ns();
   double worst = 0.0;
@@ -533,6 +559,7 @@ int ht_server_replay(ht_server *S, const void *const *ptrs, const uint64_t *lens
       r.ptr = ptrs[j];
       r.len = lens[j];
       r.pinned = pinned ? (pinned[j] ? 1 : 0) : 0;
+      r.dev_ptr = dev[j];
       r.digest_host = digests_host + j * (size_t)S->k;
       r.t_arrive = t0 + (int64_t)(arrival_us[j] * 1000.0);  // scheduled arrival
       S->reqs.push_back(r);

@@ -283,8 +283,10 @@ def test_default_launches_hash_the_previous_digest(dev):
     assert np.array_equal(_u64(d2), want2)
 
 
-def test_serving_alone_vs_mix(dev):
-    """Requests of mixed sizes (device-resident and pinned host) arrive while
+@pytest.mark.parametrize("pinned_mode", [0, 1])
+def test_serving_alone_vs_mix(dev, pinned_mode):
+    """Requests of mixed sizes (device-resident and pinned host, the latter
+    read in place by the kernel or staged through device memory) arrive while
     others are on the GPU; every digest equals the one hashed alone, and the
     oracle's on a sample."""
     from paper_2104_08865_gb300 import abi
@@ -302,7 +304,7 @@ def test_serving_alone_vs_mix(dev):
     pinned = rng.integers(0, 2, n).astype(np.int32)
     ptrs = np.where(pinned == 1, pool_host.data_ptr() + offs, pool_dev.data_ptr() + offs)
     arrivals = np.sort(rng.uniform(0, 20_000, n))
-    srv = abi.ht_server_create(h.ctx, 256 << 20, n_streams=3, max_batch=32)
+    srv = abi.ht_server_create(h.ctx, 256 << 20, n_streams=3, max_batch=32, pinned_mode=pinned_mode)
     try:
         dig = np.zeros((n, 4), dtype=np.uint64)
         abi.ht_server_replay(srv, ptrs, lens, pinned, arrivals, dig)
