@@ -606,6 +606,7 @@ def run_gpu(args):
         if sample == nbytes:
             match = all(np.array_equal(np.asarray(digests[w], dtype=np.uint64), ref[w]) for w in WIDTHS)
         cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": len(WIDTHS), "kind": "oracle",
+               "host_cores": os.cpu_count(),
                "sample": "first %d MiB of the string at each of the four widths, one oracle thread "
                          "per width (%.1f s)" % (sample >> 20, dt),
                "digests_match_gpu": match}
