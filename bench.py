@@ -190,6 +190,12 @@ def _oracle_gbs(data_np, n_bytes: int):
     return len(WIDTHS) * n_bytes / dt / 1e9, dt, out
 
 
+def _workload(nbytes: int) -> str:
+    """The benchmark's workload, as both arms name it."""
+    return ("one %d MiB string of splitmix64(%d) bytes, device-resident, hashed at widths "
+            "16/24/32/40 (seed %d) per step" % (nbytes >> 20, SEED_DATA, SEED_KEY))
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -206,16 +212,16 @@ def run_reference(args):
         _oracle_gbs(data, sample)
     dt = time.perf_counter() - t0
     gbs = args.steps * len(WIDTHS) * sample / dt / 1e9
-    desc = ("first 64 MiB of the 1 GiB splitmix64(2) string at each of the four widths per step, "
-            "one oracle thread per width")
+    desc = ("each step: the first 64 MiB of the string at each of the four widths (a bounded "
+            "sample of the workload; GB/s over the bytes hashed), one oracle thread per width")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1000 * dt / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "1 GiB string, widths 16/24/32/40 (bounded sample: 64 MiB per width)"},
+        "config": {"workload": _workload(args.bytes), "bytes_per_step": len(WIDTHS) * args.bytes},
         "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": len(WIDTHS),
-                         "kind": "oracle", "sample": desc},
+                         "host_cores": os.cpu_count(), "kind": "oracle", "sample": desc},
         "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -623,8 +629,7 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": "one %d MiB string of splitmix64(%d) bytes, device-resident, hashed "
-                                   "at widths 16/24/32/40 (seed %d) per step" % (nbytes >> 20, SEED_DATA, SEED_KEY),
+            "config": {"workload": _workload(nbytes),
                        "bytes_per_step": len(WIDTHS) * nbytes,
                        "l2": "inputs larger than L2 (no flush)",
                        "launches": "back to back on one stream" + (
