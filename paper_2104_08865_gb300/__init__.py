@@ -32,6 +32,19 @@ def digest_words(width: int) -> int:
     return width // 8
 
 
+def _device_tensor(t, name: str, dtype=None, min_numel: int = 0):
+    """Checks that t is a CUDA tensor (of dtype, with at least min_numel
+    elements) before its address reaches a kernel."""
+    if not hasattr(t, "is_cuda") or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must have dtype %s, not %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() < min_numel:
+        raise ValueError("%s holds %d elements, needs %d" % (name, t.numel(), min_numel))
+
+
 class Hasher:
     """One context: a width and an expanded seed on the current device."""
 
@@ -64,17 +77,25 @@ class Hasher:
     def hash(self, data, length: int = None, out=None, offset: int = 0, stream=None):
         """Digest of a uint8 CUDA tensor (or a byte range of it) -> int64[k] tensor."""
         import torch
-        n = data.numel() * data.element_size() - offset if length is None else length
+        _device_tensor(data, "data")
+        size = data.numel() * data.element_size()
+        n = size - offset if length is None else length
+        if offset < 0 or n < 0 or offset + n > size:
+            raise ValueError("bytes [%d, %d) outside a %d-byte tensor" % (offset, offset + n, size))
         if out is None:
             out = torch.empty(self.k, dtype=torch.int64, device=data.device)
+        _device_tensor(out, "out", torch.int64, self.k)
         _abi().ht_hash(self.ctx, data.data_ptr() + offset, n, out.data_ptr(),
                     stream if stream is not None else torch.cuda.current_stream())
         return out
 
     def hash_batch(self, ptrs_dev, lens_dev, count: int, out=None, stream=None):
         import torch
+        _device_tensor(ptrs_dev, "ptrs_dev", torch.int64, count)
+        _device_tensor(lens_dev, "lens_dev", torch.int64, count)
         if out is None:
             out = torch.empty((count, self.k), dtype=torch.int64, device=ptrs_dev.device)
+        _device_tensor(out, "out", torch.int64, count * self.k)
         _abi().ht_hash_batch(self.ctx, ptrs_dev.data_ptr(), lens_dev.data_ptr(), count,
                           out.data_ptr(), stream if stream is not None else torch.cuda.current_stream())
         return out
@@ -150,6 +171,7 @@ class Incremental:
             _abi().ht_inc_update_host(self.h, data.ctypes.data if data.size else None, data.size,
                                       self._stream(stream))
         else:
+            _device_tensor(data, "data")
             n = data.numel() * data.element_size()
             _abi().ht_inc_update(self.h, data.data_ptr() if n else None, n, self._stream(stream))
 
@@ -212,6 +234,7 @@ class Table:
         CUDA int32 tensor holding uint32 ids) or None."""
         import torch
         count = digests.shape[0]
+        _device_tensor(digests, "digests", torch.int64, count * self.k)
         out = torch.empty(count, dtype=torch.int32, device=digests.device) if rep else None
         _abi().ht_table_insert(self.t, digests, count, out, self._stream(stream))
         return out
@@ -221,6 +244,7 @@ class Table:
         as int32, where none)."""
         import torch
         count = digests.shape[0]
+        _device_tensor(digests, "digests", torch.int64, count * self.k)
         out = torch.empty(count, dtype=torch.int32, device=digests.device)
         _abi().ht_table_find(self.t, digests, count, out, self._stream(stream))
         return out

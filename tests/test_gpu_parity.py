@@ -233,6 +233,33 @@ def test_launch_counter_counts_kernels(dev):
     assert h.launches() - before == 1 + {0: 4, 1: 5, 2: 3}[batch_kernel]
 
 
+def test_python_layer_rejects_bad_tensors(dev):
+    """The convenience layer checks tensors before their addresses reach a
+    kernel: host tensors, wrong dtypes and ranges past the end are refused."""
+    from paper_2104_08865_gb300 import Table
+    h, _ = _pair(16)
+    d = torch.zeros(1000, dtype=torch.uint8, device=dev)
+    with pytest.raises(ValueError):
+        h.hash(torch.zeros(1000, dtype=torch.uint8))  # host tensor
+    with pytest.raises(ValueError):
+        h.hash(d, length=1001)
+    with pytest.raises(ValueError):
+        h.hash(d, length=10, offset=995)
+    ptrs = torch.tensor([d.data_ptr()], dtype=torch.int64, device=dev)
+    with pytest.raises(ValueError):
+        h.hash_batch(ptrs, torch.tensor([10], dtype=torch.int32, device=dev), 1)
+    with pytest.raises(ValueError):
+        h.hash_batch(ptrs, torch.tensor([10], dtype=torch.int64, device=dev), 2)
+    with h.incremental() as inc:
+        with pytest.raises(ValueError):
+            inc.update(torch.zeros(10, dtype=torch.uint8))
+    with Table(h, max_entries=4) as t:
+        with pytest.raises(ValueError):
+            t.insert(torch.zeros((2, 2), dtype=torch.int64))
+    # the valid forms still work
+    assert h.hash(d, length=10, offset=990).shape == (2,)
+
+
 @pytest.mark.parametrize("width", WIDTHS)
 def test_rekey_matches_fresh_context(dev, width):
     from paper_2104_08865_gb300 import abi
