@@ -13,6 +13,7 @@ the four hashes (4 GiB hashed).  The input is larger than L2 (1 GiB vs
   roofline  the dominant kernel (the slowest width) against the measured HBM
           copy bandwidth; algorithmic bytes = 2^30 read per launch.
   cpu_baseline  the CPU oracle on the same bytes (one thread per width).
+  blocks_256  the same string and widths with 256-bit blocks (b = 4 words).
 
 `--impl reference` times the CPU oracle instead (the reference arm): each step
 hashes a bounded sample (the first 64 MiB of the string at each width).
@@ -415,6 +416,64 @@ def run_incremental(args, dev, stream, data, want):
     return res
 
 
+def run_v3(args, dev, stream, data):
+    """The 256-bit-block variant (blocks of 4 words, width | HT_BLOCK_256) on the
+    benchmark string: each width timed alone (CUDA events around each launch,
+    default launch shape), then the four launches back to back with overlap,
+    as in the main step."""
+    import numpy as np
+    import torch
+
+    from paper_2104_08865_gb300 import Hasher, abi
+    nbytes = args.bytes
+    hs = {w: Hasher(w | abi.HT_BLOCK_256, seed_words=abi.ht_seed_expand(SEED_KEY, w | abi.HT_BLOCK_256))
+          for w in WIDTHS}
+    outs = {w: torch.empty(w // 8, dtype=torch.int64, device=dev) for w in WIDTHS}
+
+    def step(evs=None):
+        for i, w in enumerate(WIDTHS):
+            if evs is not None:
+                evs[i][0].record(stream)
+            abi.ht_hash(hs[w].ctx, data.data_ptr(), nbytes, outs[w].data_ptr(), stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    reps = 30
+    solo = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+             for _ in WIDTHS] for _ in range(reps)]
+    for ev in solo:
+        step(ev)
+    torch.cuda.synchronize()
+    per_w = {w: statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for ev in solo)
+             for i, w in enumerate(WIDTHS)}
+    for w in WIDTHS:
+        abi.ht_ctx_set_flags(hs[w].ctx, abi.HT_FLAG_OVERLAP_LAUNCHES)
+    for _ in range(3):
+        step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    peak, _ = _peaks()
+    dom = max(WIDTHS, key=lambda w: per_w[w])
+    res = {"workload": _workload(nbytes).replace("hashed at widths", "256-bit blocks, widths"),
+           "step_gbs": round(len(WIDTHS) * nbytes / ms / 1e6, 1), "ms_per_step": round(ms, 4),
+           "per_width_gbs": {str(w): round(nbytes / per_w[w] / 1e6, 1) for w in WIDTHS},
+           "dominant_frac_of_peak": round(nbytes / per_w[dom] / 1e6 / peak, 4),
+           "shape": abi.ht_get_shape(hs[dom].ctx, nbytes),
+           "digests": {str(w): ["%016x" % v for v in outs[w].cpu().numpy().view(np.uint64)] for w in WIDTHS}}
+    for h in hs.values():
+        h.close()
+    return res
+
+
 def run_serving(args, dev, stream):
     """C5: Poisson arrivals of width-32 hash requests, lengths log-uniform in
     [256 B, 64 MiB], 16 GiB admission budget; offered load swept over
@@ -617,6 +676,7 @@ def run_gpu(args):
                          "per width (%.1f s)" % (sample >> 20, dt),
                "digests_match_gpu": match}
 
+    v3 = run_v3(args, dev, stream, data) if (rank == 0 and not args.no_v3) else None
     batch = run_batch(args, dev, stream) if not args.no_batch else None
     incremental = (run_incremental(args, dev, stream, data, digests[24])
                    if (rank == 0 and not args.no_inc) else None)
@@ -645,6 +705,7 @@ def run_gpu(args):
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": ck,
             "shapes": shapes,
             "batch": batch, "incremental": incremental, "dedup": dedup, "serving": serving,
+            "blocks_256": v3,
             "digests": {str(w): ["%016x" % v for v in digests[w]] for w in WIDTHS},
         }
         print(json.dumps(line), flush=True)
@@ -675,6 +736,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-inc", action="store_true", help="skip the incremental-hashing leg")
     ap.add_argument("--no-dedup", action="store_true", help="skip the deduplication leg")
+    ap.add_argument("--no-v3", action="store_true", help="skip the 256-bit-block leg")
     ap.add_argument("--batch-strings", type=int, default=50_000)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0)

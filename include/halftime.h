@@ -42,7 +42,7 @@ typedef struct ht_table ht_table;
 /* ---- status codes -------------------------------------------------------- */
 #define HT_OK 0
 #define HT_ERR_ARG -1      /* invalid argument (NULL pointer, size mismatch) */
-#define HT_ERR_WIDTH -2    /* width not in {16, 24, 32, 40} */
+#define HT_ERR_WIDTH -2    /* width not in {16, 24, 32, 40} (optionally | HT_BLOCK_256) */
 #define HT_ERR_TOO_LONG -3 /* input or batch exceeds the context's capacity */
 #define HT_ERR_CUDA -4     /* a CUDA runtime call failed (message has detail) */
 #define HT_ERR_NOMEM -5    /* device or host allocation failed */
@@ -64,6 +64,23 @@ int ht_last_error(char *buf, size_t n);
  * the length word.  Widths 16/24/32/40 give 2865/4245/5598/6897 words.
  * Returns 0 for an unsupported width. */
 size_t ht_seed_words(int width_bytes);
+
+/* ---- block size: 512-bit (default) or 256-bit blocks --------------------
+ * Every width_bytes argument above and below may carry HT_BLOCK_256
+ * (width_bytes | HT_BLOCK_256) to select blocks of b = 4 64-bit words instead
+ * of the default b = 8 (Section 2, blocks of b words; Section 6.3, where the
+ * 256-bit-block build is labelled "v3": the block size of processors
+ * without 512-bit vectors).  With b = 4 an execution holds 8*4*d*w bytes
+ * (672 / 672 / 480 bytes for widths 24 / 32 / 40 and 576 for width 16), the
+ * tree runs over 4 lanes per output word, and the seed layout shrinks to
+ * E, T, F = k*19*8*4 and R = 4*d*w + k words: 1577 / 2337 / 3082 / 3797
+ * words for widths 16 / 24 / 32 / 40.  Digests differ from those of 8-word
+ * blocks.  A context created with HT_BLOCK_256 serves ht_hash, ht_hash_host,
+ * ht_hash_batch, ht_hash_batch_naive, the server and the digest table, with
+ * the warp-chunk kernel only (ht_set_shape accepts kernel 1 with
+ * chunk_levels 2; ht_autotune tunes its launch size); ht_inc_create,
+ * ht_part_begin and ht_hash_noalloc reject it with HT_ERR_WIDTH. */
+#define HT_BLOCK_256 0x100
 
 /* Expands a 64-bit seed into the seed words of a width on the host: word i
  * is the i-th output of splitmix64 (Steele, Lea, Flood, OOPSLA 2014) started
@@ -179,17 +196,20 @@ int ht_hash_batch_naive(ht_ctx *ctx, const void *const *ptrs_host,
  * (ht_part_merge) and ht_finish_parts on one of them.  Calls on a context are
  * stream-ordered like the others. */
 
-/* Bytes per split unit: parts start and end on multiples of this. */
+/* Bytes per split unit: parts start and end on multiples of this (0 for a
+ * context of 256-bit blocks, which does not split strings). */
 uint64_t ht_part_granule(ht_ctx *ctx);
 
-/* Size in 64-bit words of the part state of a string of total_len bytes. */
+/* Size in 64-bit words of the part state of a string of total_len bytes (0
+ * for a context of 256-bit blocks). */
 size_t ht_part_state_words(ht_ctx *ctx, uint64_t total_len);
 
 /* Opens (and zeroes, on `stream`) the part state for a string of total_len
  * bytes.  state_dev: a device buffer of at least ht_part_state_words words
  * that the caller owns and keeps alive until ht_finish_parts (for example a
  * tensor it will all-reduce), or NULL for a buffer the context allocates.
- * Errors: HT_ERR_ARG (buffer too small), HT_ERR_NOMEM, HT_ERR_CUDA. */
+ * Errors: HT_ERR_ARG (buffer too small), HT_ERR_WIDTH (a context of 256-bit
+ * blocks), HT_ERR_NOMEM, HT_ERR_CUDA. */
 int ht_part_begin(ht_ctx *ctx, uint64_t total_len, void *state_dev, size_t words,
                   ht_stream_t stream);
 
@@ -240,7 +260,8 @@ int ht_finish_parts(ht_ctx *ctx, uint64_t *digest_dev, ht_stream_t stream);
 
 /* Creates a handle (1.3 to 3.1 MB of device memory by width; host updates add
  * two staging slots of 1024 chunks) with an open, empty string.
- * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ * Errors: HT_ERR_ARG, HT_ERR_WIDTH (a context of 256-bit blocks),
+ * HT_ERR_CUDA. */
 int ht_inc_create(ht_ctx *ctx, ht_inc **out);
 int ht_inc_destroy(ht_inc *h);
 
@@ -372,7 +393,8 @@ int ht_table_status(ht_table *t, ht_stream_t stream);
  *   - Every call shares the one array and clears the parts it uses at the
  *     start, so calls that overlap on the GPU (other streams, other host
  *     threads) race and give wrong digests: order them.
- * Errors: HT_ERR_WIDTH, HT_ERR_ARG, HT_ERR_TOO_LONG, HT_ERR_CUDA. */
+ * Errors: HT_ERR_WIDTH (also for width_bytes | HT_BLOCK_256), HT_ERR_ARG,
+ * HT_ERR_TOO_LONG, HT_ERR_CUDA. */
 int ht_hash_noalloc(int width_bytes, const uint64_t *seed_words_host,
                     size_t n_words, const void *data_dev, uint64_t len,
                     uint64_t *digest_dev, ht_stream_t stream);

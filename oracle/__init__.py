@@ -82,13 +82,14 @@ def _bytes_ptr(data):
     return arr.ctypes.data_as(ctypes.c_void_p), arr.size, arr
 
 
-def params(width: int) -> dict:
+def params(width: int, b: int = 8) -> dict:
+    """d, e, k, w of a width and the bytes of one execution with blocks of b words."""
     d, e, k, w, xb = (ctypes.c_int() for _ in range(5))
     rc = lib().htref_params(width, ctypes.byref(d), ctypes.byref(e), ctypes.byref(k),
                             ctypes.byref(w), ctypes.byref(xb))
     if rc:
         raise ValueError("bad width %r" % width)
-    return dict(d=d.value, e=e.value, k=k.value, w=w.value, exec_bytes=xb.value)
+    return dict(d=d.value, e=e.value, k=k.value, w=w.value, exec_bytes=8 * b * d.value * w.value)
 
 
 def seed_words(width: int, b: int = 8, f: int = 8) -> int:
@@ -145,8 +146,9 @@ def hash_bytes(width: int, seeds: np.ndarray, data, *, b: int = 8, f: int = 8,
     return dig
 
 
-def hash_many(width: int, seeds: np.ndarray, buf: np.ndarray, offsets, lengths) -> np.ndarray:
-    """Digests of slices buf[offsets[i] : offsets[i]+lengths[i]] -> uint64[count, k]."""
+def hash_many(width: int, seeds: np.ndarray, buf: np.ndarray, offsets, lengths, b: int = 8) -> np.ndarray:
+    """Digests of slices buf[offsets[i] : offsets[i]+lengths[i]] -> uint64[count, k]
+    (blocks of b words: 8, or 4 for the 256-bit-block variant)."""
     p = params(width)
     seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
     buf = np.ascontiguousarray(buf).view(np.uint8).reshape(-1)
@@ -158,8 +160,9 @@ def hash_many(width: int, seeds: np.ndarray, buf: np.ndarray, offsets, lengths) 
         o = int(o); n = int(n)
         assert o + n <= buf.size
         row = out[i]
-        rc = L.htref_hash(width, sp, seeds.size, ctypes.c_void_p(base + o) if n else None,
-                          n, row.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        rc = L.htref_hash_bf(width, b, 8, 0, sp, seeds.size,
+                             ctypes.c_void_p(base + o) if n else None, n,
+                             row.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), None)
         if rc:
             raise ValueError("htref_hash failed: %d" % rc)
     return out

@@ -29,7 +29,8 @@ def _abi():
 
 
 def digest_words(width: int) -> int:
-    return width // 8
+    """Digest words k of a width code (16/24/32/40, optionally | HT_BLOCK_256)."""
+    return (width & 0xFF) // 8
 
 
 def _device_tensor(t, name: str, dtype=None, min_numel: int = 0):
@@ -46,13 +47,15 @@ def _device_tensor(t, name: str, dtype=None, min_numel: int = 0):
 
 
 class Hasher:
-    """One context: a width and an expanded seed on the current device."""
+    """One context: a width and an expanded seed on the current device.
+    width: 16, 24, 32 or 40, or that value | abi.HT_BLOCK_256 for blocks of
+    four words (the 256-bit-block variant)."""
 
     def __init__(self, width: int, seed64: int = None, seed_words=None, stream=None):
         if seed_words is None:
             seed_words = _abi().ht_seed_expand(seed64 if seed64 is not None else 0, width)
         self.width = width
-        self.k = width // 8
+        self.k = digest_words(width)
         self.seed_words = np.ascontiguousarray(seed_words, dtype=np.uint64)
         self.ctx = _abi().ht_ctx_create(width, self.seed_words, stream)
 

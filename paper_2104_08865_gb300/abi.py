@@ -33,6 +33,8 @@ HT_ERR_TIMEOUT = -7
 HT_ERR_BUSY = -8
 HT_ERR_DEVICE = -9
 WIDTHS = (16, 24, 32, 40)
+# width_bytes | HT_BLOCK_256 selects blocks of 4 words (256 bits) instead of 8
+HT_BLOCK_256 = 0x100
 
 
 class HalftimeError(RuntimeError):
@@ -310,7 +312,7 @@ def ht_inc_import(h: int, state: bytes, stream=None) -> None:
 
 
 def ht_short_hash_keys(seed64: int, width: int) -> np.ndarray:
-    out = np.zeros(2 * (width // 8) + 1, dtype=np.uint64)
+    out = np.zeros(2 * ((width & 0xFF) // 8) + 1, dtype=np.uint64)
     _check(_lib.ht_short_hash_keys(seed64, width, out.ctypes.data_as(_u64p), out.size))
     return out
 
@@ -347,7 +349,7 @@ def ht_table_slot_bits(t: int) -> int:
 
 
 def ht_table_keys(t: int, width: int) -> np.ndarray:
-    out = np.zeros(2 * (width // 8) + 1, dtype=np.uint64)
+    out = np.zeros(2 * ((width & 0xFF) // 8) + 1, dtype=np.uint64)
     _check(_lib.ht_table_keys(t, out.ctypes.data_as(_u64p), out.size))
     return out
 

@@ -14,6 +14,7 @@
 #include "halftime.h"
 #include "ht_internal.h"
 #include "ht_runtime.h"
+#include "ht_spec.cuh"
 
 namespace ht {
 
@@ -48,6 +49,10 @@ const KernelSet *kernel_set(int width) {
     case 24: return &kernels_w24();
     case 32: return &kernels_w32();
     case 40: return &kernels_w40();
+    case 16 | HT_BLOCK_256: return &kernels_w16_v3();
+    case 24 | HT_BLOCK_256: return &kernels_w24_v3();
+    case 32 | HT_BLOCK_256: return &kernels_w32_v3();
+    case 40 | HT_BLOCK_256: return &kernels_w40_v3();
     default: return nullptr;
   }
 }
@@ -63,8 +68,9 @@ uint64_t splitmix64_next(uint64_t *state) {
 
 // ---- tree bookkeeping on the host -------------------------------------------------
 
-uint64_t items_of(uint64_t N, int L) {
-  const uint64_t it = (N + (1ull << (3 * L)) - 1) >> (3 * L);
+uint64_t items_of(uint64_t N, int L, int lanes) {
+  const uint64_t ch = (uint64_t)(8 / lanes) << (3 * L);  // executions per item
+  const uint64_t it = (N + ch - 1) / ch;
   return it ? it : 1;
 }
 
@@ -207,10 +213,12 @@ static ht_shape default_shape() {
   return s;
 }
 
-static bool shape_ok(const ht_shape &s) {
+static bool shape_ok(const KernelSet &ks, const ht_shape &s) {
   if (s.threads_per_block < 32 || s.threads_per_block % 32 != 0 || s.blocks_per_sm < 1 ||
       s.blocks_per_sm > 32)
     return false;
+  // 256-bit blocks: the warp-chunk kernel with 64-execution sub-chunks only
+  if (ks.lanes != kLanes) return s.kernel == 1 && s.chunk_levels == 2 && s.threads_per_block <= 256;
   if (s.kernel == 0) return s.stages >= 2 && s.stages <= 8 && s.threads_per_block <= 256;
   if (s.kernel == 1)
     return s.chunk_levels >= 1 && s.chunk_levels <= 3 && s.threads_per_block <= 256;
@@ -218,12 +226,14 @@ static bool shape_ok(const ht_shape &s) {
 }
 
 // Work units of a string for a shape: stream/range units (8 executions each,
-// plus the tail unit) or warp-chunk items (8^L executions each, at least one).
-static uint64_t units_for(const ht_shape &s, uint64_t N) {
-  return s.kernel != 1 ? ((N + 7) >> 3) + 1 : items_of(N, s.chunk_levels);
+// plus the tail unit) or warp-chunk items (8^L executions each, two
+// 64-execution sub-chunks with 256-bit blocks; at least one).
+static uint64_t units_for(const KernelSet &ks, const ht_shape &s, uint64_t N) {
+  return s.kernel != 1 ? ((N + 7) >> 3) + 1 : items_of(N, s.chunk_levels, ks.lanes);
 }
 static uint64_t unit_bytes(const KernelSet &ks, const ht_shape &s) {
-  return (uint64_t)ks.exec_bytes << (s.kernel != 1 ? 3 : 3 * s.chunk_levels);
+  if (s.kernel != 1) return (uint64_t)ks.exec_bytes << 3;
+  return ((uint64_t)ks.exec_bytes * (uint64_t)(kLanes / ks.lanes)) << (3 * s.chunk_levels);
 }
 static uint64_t groups_for(const ht_shape &s, uint64_t N) {
   return groups_of(N, s.kernel != 1 ? 1 : s.chunk_levels);
@@ -355,9 +365,9 @@ int ht_ctx_create(int width, const uint64_t *seed_words, size_t n_words, ht_stre
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   int optin = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && ks->stream_single)
     e = cudaFuncSetAttribute(ks->stream_single, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && ks->stream_batch)
     e = cudaFuncSetAttribute(ks->stream_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   c->smem_optin = optin;
   if (e != cudaSuccess) {
@@ -440,7 +450,7 @@ int ht_hash(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest, ht_stre
   sp.n_exec = len / (uint64_t)c->ks->exec_bytes;
   sp.item0 = 0;
   sp.grp0 = 0;
-  const uint64_t n_units = units_for(shape, sp.n_exec);
+  const uint64_t n_units = units_for(*c->ks, shape, sp.n_exec);
   if (n_units > 0xffffffffull) return set_error(HT_ERR_TOO_LONG, "string too long for one launch");
   sp.n_items = (uint32_t)n_units;
   sp.pad = 0;
@@ -481,7 +491,7 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
   sp.n_exec = len / B;
   sp.item0 = 0;
   sp.grp0 = 0;
-  const uint64_t n_units = units_for(shape, sp.n_exec);
+  const uint64_t n_units = units_for(ks, shape, sp.n_exec);
   if (n_units > 0xffffffffull) return set_error(HT_ERR_TOO_LONG, "string too long for one launch");
   sp.n_items = (uint32_t)n_units;
   sp.pad = 0;
@@ -685,7 +695,7 @@ int ht_get_shape(ht_ctx *c, uint64_t len, ht_shape *out) {
 }
 
 int ht_set_shape(ht_ctx *c, uint64_t len, const ht_shape *shape) {
-  if (!c || !shape || !shape_ok(*shape)) return set_error(HT_ERR_ARG, "ht_set_shape: bad shape");
+  if (!c || !shape || !shape_ok(*c->ks, *shape)) return set_error(HT_ERR_ARG, "ht_set_shape: bad shape");
   c->shapes[bucket_of(len)] = *shape;
   return HT_OK;
 }
@@ -696,7 +706,9 @@ int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
   if (!c || len == UINT64_MAX) return set_error(HT_ERR_ARG, "ht_autotune: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   const KernelSet &ks = *c->ks;
-  // candidate shapes of both kernel families that fit the device
+  // candidate shapes of the three kernel families that fit the device (the
+  // warp-chunk kernel with 64-execution sub-chunks only, for 256-bit blocks)
+  const bool v3 = ks.lanes != kLanes;
   std::vector<ht_shape> cands;
   for (int warps : {2, 3, 4, 5, 6, 8})
     for (int stages : {2, 3, 4, 6})
@@ -706,6 +718,7 @@ int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
         h.stages = stages;
         h.threads_per_block = 32 * warps;
         h.blocks_per_sm = bps;
+        if (v3) continue;
         const size_t smem = stream_smem(ks, h);
         if ((int)smem > c->smem_optin) continue;
         if (occupancy(ks.stream_single, h.threads_per_block, smem) < bps) continue;
@@ -717,7 +730,7 @@ int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
       h.kernel = 2;
       h.threads_per_block = tpb;
       h.blocks_per_sm = bps;
-      if (occupancy(ks.range_single, tpb, 0) < bps) continue;
+      if (v3 || occupancy(ks.range_single, tpb, 0) < bps) continue;
       cands.push_back(h);
     }
   for (int L : {2, 3})
@@ -728,7 +741,7 @@ int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
         h.chunk_levels = L;
         h.threads_per_block = tpb;
         h.blocks_per_sm = bps;
-        if (occupancy(ks.single_aligned[L - 1], tpb, 0) < bps) continue;
+        if (!ks.single_aligned[L - 1] || occupancy(ks.single_aligned[L - 1], tpb, 0) < bps) continue;
         cands.push_back(h);
       }
   uint8_t *buf = nullptr;

@@ -120,11 +120,20 @@ struct KernelSet {
   const void *inc_unaligned;
   const void *inc_stack;      // incremental: pending stack nodes into the sum
   int exec_bytes, k, n_seed, off_T, off_F, off_R, ew;
+  // words per block: 8, or 4 for the 256-bit-block variant, whose set holds
+  // only the warp-chunk kernels with 64-execution sub-chunks (index L = 2)
+  // and the multi-block planner; its other entries are null
+  int lanes;
 };
 
 const KernelSet &kernels_w16();
 const KernelSet &kernels_w24();
 const KernelSet &kernels_w32();
 const KernelSet &kernels_w40();
+// the same widths with 256-bit blocks
+const KernelSet &kernels_w16_v3();
+const KernelSet &kernels_w24_v3();
+const KernelSet &kernels_w32_v3();
+const KernelSet &kernels_w40_v3();
 
 }  // namespace ht

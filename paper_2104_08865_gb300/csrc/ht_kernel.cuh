@@ -19,6 +19,10 @@
 // straight into the string's final-NH sum (Section 5.2).  The warp that
 // finishes a string's last work item adds the Toeplitz tail NH (Section 6.1)
 // and writes the digest.  No kernel ever spins on another warp.
+// With 256-bit blocks (template parameter B = 4, the block size of the
+// paper's "v3" build, Section 6.3; L = 2 only) a work item is two
+// 64-execution sub-chunks, one per half-warp, and thread (x, p) of a half is
+// x = (lane >> 1) & 7, p = lane & 1.
 #pragma once
 
 #include "ht_internal.h"
@@ -45,11 +49,26 @@ __device__ __forceinline__ uint64_t warp_sum(uint64_t v) {
   return v;
 }
 
-// Sum over the eight x-threads that share p (lane bits 2..4).
+// Thread roles in a warp for blocks of B words.  B = 8: thread (x, p),
+// x = lane >> 2, p = lane & 3, owns block lanes 2p and 2p+1 of its
+// executions.  B = 4 (256-bit blocks): the half-warps h = lane >> 4 take
+// consecutive 64-execution sub-chunks, and in each thread (x, p),
+// x = (lane >> 1) & 7, p = lane & 1, owns block lanes 2p and 2p+1.
+template <int B>
+__device__ __forceinline__ int lane_x(int ln) { return B == 8 ? ln >> 2 : (ln >> 1) & 7; }
+template <int B>
+__device__ __forceinline__ int lane_p(int ln) { return B == 8 ? ln & 3 : ln & 1; }
+template <int B>
+__device__ __forceinline__ int lane_h(int ln) { return B == 8 ? 0 : ln >> 4; }
+
+// Sum over the eight x-threads that share (h, p): lane bits 2..4 for B = 8,
+// lane bits 1..3 for B = 4.
+template <int B = kLanes>
 __device__ __forceinline__ uint64_t x_sum(uint64_t v) {
-  v += __shfl_xor_sync(kFull, v, 4);
-  v += __shfl_xor_sync(kFull, v, 8);
-  v += __shfl_xor_sync(kFull, v, 16);
+  constexpr int s = B == 8 ? 4 : 2;
+  v += __shfl_xor_sync(kFull, v, s);
+  v += __shfl_xor_sync(kFull, v, 2 * s);
+  v += __shfl_xor_sync(kFull, v, 4 * s);
   return v;
 }
 
@@ -164,15 +183,16 @@ __device__ __forceinline__ uint64_t combine(int t, const uint64_t (&h)[E]) {
 
 // One EHC execution for block lanes 2p and 2p+1 (Section 3.3, Section 5.1):
 // Encode (systematic GF(8) code, XOR only), Hash (NH of every encoded word
-// under its own key E[c*3+u]), Combine (y = T h over Z_{2^64}).
-template <int W, bool ALIGNED>
+// under its own key E[c*3+u]), Combine (y = T h over Z_{2^64}).  Blocks are
+// B words (8 B bytes) long.
+template <int W, bool ALIGNED, int B = kLanes>
 __device__ __forceinline__ void ehc2(const uint8_t *ex, int p, uint32_t sh,
                                      const KParams &P, uint64_t (&y)[2][Spec<W>::k]) {
   using S = Spec<W>;
   constexpr int d = S::d, e = S::e, k = S::k, np = e - d, dw = d * kItemWords;
   uint4 v[dw];
 #pragma unroll
-  for (int b = 0; b < dw; ++b) v[b] = ld16<ALIGNED>(ex + b * 64 + p * 16, sh);
+  for (int b = 0; b < dw; ++b) v[b] = ld16<ALIGNED>(ex + b * (8 * B) + p * 16, sh);
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
     uint32_t lo[dw], hi[dw];
@@ -216,21 +236,21 @@ template <int W>
 __device__ __forceinline__ uint64_t tree_key(const KParams &P, int t, int lvl, int i) {
   return __ldg(P.seeds + Dims<W>::off_T + (t * kLevels + lvl) * (kFan - 1) + i);
 }
-template <int W>
+template <int W, int B = kLanes>
 __device__ __forceinline__ uint64_t final_key(const KParams &P, int t, int lvl, uint64_t j, int lane) {
-  return __ldg(P.seeds + Dims<W>::off_F + ((t * kLevels + lvl) * kFan + (int)j) * kLanes + lane);
+  return __ldg(P.seeds + Dims<W, B>::off_F + ((t * kLevels + lvl) * kFan + (int)j) * B + lane);
 }
 
 // ---- the finaliser: pending-root sum + Toeplitz tail (Section 6.1) ----------
 
 // The Toeplitz tail NH of the string, length word included (Section 6.1, and
 // reading 9), summed over the warp: every lane gets the k sums.
-template <int W>
+template <int W, int B = kLanes>
 __device__ __forceinline__ void tail_sum(const KParams &P, const StrPlan &sp, int ln,
                                          uint64_t (&sum)[Spec<W>::k]) {
   constexpr int k = Spec<W>::k;
-  constexpr int B = Dims<W>::exec_bytes;
-  const uint64_t tstart = sp.n_exec * (uint64_t)B;
+  constexpr int XB = Dims<W, B>::exec_bytes;
+  const uint64_t tstart = sp.n_exec * (uint64_t)XB;
   const uint64_t tlen = sp.len - tstart;  // < B
   const uint32_t M = (uint32_t)((tlen + 7) / 8);
 #pragma unroll
@@ -244,13 +264,13 @@ __device__ __forceinline__ void tail_sum(const KParams &P, const StrPlan &sp, in
       word = tail_word(sp.ptr + tstart + 8ull * m, rem < 8 ? (uint32_t)rem : 8u);
     }
 #pragma unroll
-    for (int t = 0; t < k; ++t) sum[t] += nh64(word, __ldg(P.seeds + Dims<W>::off_R + t + m));
+    for (int t = 0; t < k; ++t) sum[t] += nh64(word, __ldg(P.seeds + Dims<W, B>::off_R + t + m));
   }
 #pragma unroll
   for (int t = 0; t < k; ++t) sum[t] = warp_sum(sum[t]);
 }
 
-template <int W>
+template <int W, int B = kLanes>
 __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx, int ln) {
   constexpr int k = Spec<W>::k;
   __threadfence();
@@ -258,7 +278,7 @@ __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx
 #pragma unroll
   for (int t = 0; t < k; ++t) acc[t] = ld_cg(P.scr.str_acc + (uint64_t)sidx * k + t);
   uint64_t sum[k];
-  tail_sum<W>(P, sp, ln, sum);
+  tail_sum<W, B>(P, sp, ln, sum);
   if (ln == 0) {
 #pragma unroll
     for (int t = 0; t < k; ++t) {
@@ -272,12 +292,12 @@ __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx
 // A string with a single work item: its warp holds the whole final-NH sum
 // (pend, spread over the lanes), so it writes the digest without the
 // string's scratch sum and completion count.
-template <int W>
+template <int W, int B = kLanes>
 __device__ void finish_local(const KParams &P, const StrPlan &sp, unsigned sidx,
                              uint64_t (&pend)[Spec<W>::k], int ln) {
   constexpr int k = Spec<W>::k;
   uint64_t sum[k];
-  tail_sum<W>(P, sp, ln, sum);
+  tail_sum<W, B>(P, sp, ln, sum);
 #pragma unroll
   for (int t = 0; t < k; ++t) sum[t] += warp_sum(pend[t]);
   if (ln == 0)
@@ -296,14 +316,17 @@ constexpr uint64_t kNoNode = ~0ull;
 // 2p and 2p+1); the leaves and nodes of the string's last, incomplete chunk
 // are pending roots, whose final NH goes into pend.  Returns whether the
 // chunk is full.  Touches no scratch.
-template <int W, int L, bool ALIGNED>
+// With 256-bit blocks (B = 4, L = 2) a work item is two 64-execution
+// sub-chunks, one per half-warp: half h returns level-2 node 2c + h.
+template <int W, int L, bool ALIGNED, int B = kLanes>
 __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, const uint8_t *base,
                                            uint64_t c, int ln, uint64_t (&pend)[Spec<W>::k], bool &anyp,
                                            uint64_t &v0, uint64_t &v1) {
+  static_assert(B == 8 || L == 2, "256-bit blocks take 64-execution sub-chunks");
   constexpr int k = Spec<W>::k;
-  constexpr uint64_t B = Dims<W>::exec_bytes;
-  constexpr uint64_t CH = 1ull << (3 * L);
-  const int x = ln >> 2, p = ln & 3;
+  constexpr uint64_t XB = Dims<W, B>::exec_bytes;
+  constexpr uint64_t CH = (uint64_t)(8 / B) << (3 * L);  // executions per work item
+  const int x = lane_x<B>(ln), p = lane_p<B>(ln), h = lane_h<B>(ln);
   const uint64_t N = sp.n_exec;
   const uint32_t sh = ALIGNED ? 0u : (uint32_t)(((uintptr_t)base) & 15u);
   const bool full = c * CH < N && (N - c * CH) >= CH;
@@ -319,7 +342,7 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
       // eight executions, one per x-thread; level 1 across the x-threads
       const int m = (int)((N - e0) < 8 ? (N - e0) : 8);
       uint64_t y[2][k];
-      if (x < m) ehc2<W, ALIGNED>(base + (e0 + (uint64_t)x) * B, p, sh, P, y);
+      if (x < m) ehc2<W, ALIGNED>(base + (e0 + (uint64_t)x) * XB, p, sh, P, y);
       if (full) {
 #pragma unroll
         for (int t = 0; t < k; ++t) {
@@ -339,9 +362,10 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
     constexpr int NSUB = (L == 3) ? 8 : (L == 2 ? 1 : 0);
 #pragma unroll 1
     for (int sub = 0; sub < NSUB; ++sub) {
-      const uint64_t sb = e0 + 64ull * sub;
-      if (sb >= N) break;
-      const int m = (int)((N - sb) < 64 ? (N - sb) : 64);
+      const uint64_t sb = e0 + 64ull * (sub + h);
+      // (with B = 4 both half-warps stay for the shuffles below)
+      if (B == 8 && sb >= N) break;
+      const int m = sb >= N ? 0 : (int)((N - sb) < 64 ? (N - sb) : 64);
       int cnt = m - 8 * x;
       cnt = cnt < 0 ? 0 : (cnt > 8 ? 8 : cnt);
       uint64_t n1[2][k];
@@ -349,14 +373,14 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
       for (int l = 0; l < 2; ++l)
 #pragma unroll
         for (int t = 0; t < k; ++t) n1[l][t] = 0;
-      const uint8_t *ex = base + (sb + 8ull * x) * B;
+      const uint8_t *ex = base + (sb + 8ull * x) * XB;
       if (cnt == 8) {
         // eight leaves -> one level-1 node per (tree, lane), in registers;
         // two executions per iteration keep two loads batches in flight
 #pragma unroll 2
         for (int s = 0; s < 8; ++s) {
           uint64_t y[2][k];
-          ehc2<W, ALIGNED>(ex + s * B, p, sh, P, y);
+          ehc2<W, ALIGNED, B>(ex + s * XB, p, sh, P, y);
 #pragma unroll
           for (int l = 0; l < 2; ++l)
 #pragma unroll
@@ -368,15 +392,52 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
 #pragma unroll 1
         for (int s = 0; s < cnt; ++s) {
           uint64_t y[2][k];
-          ehc2<W, ALIGNED>(ex + s * B, p, sh, P, y);
+          ehc2<W, ALIGNED, B>(ex + s * XB, p, sh, P, y);
 #pragma unroll
           for (int t = 0; t < k; ++t)
-            pend[t] += nh64(y[0][t], final_key<W>(P, t, 0, s, 2 * p)) +
-                       nh64(y[1][t], final_key<W>(P, t, 0, s, 2 * p + 1));
+            pend[t] += nh64(y[0][t], final_key<W, B>(P, t, 0, s, 2 * p)) +
+                       nh64(y[1][t], final_key<W, B>(P, t, 0, s, 2 * p + 1));
           anyp = true;
         }
       }
-      if (m == 64) {
+      if constexpr (B == 4) {
+        // two sub-chunks, one per half-warp: the shuffles of level 2 run in
+        // both halves whenever either half completes its level-2 node
+        if (__any_sync(kFull, m == 64)) {
+          uint64_t n2[2][k];
+#pragma unroll
+          for (int t = 0; t < k; ++t) {
+            const uint64_t key = x < 7 ? tree_key<W>(P, t, 1, x) : 0;
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+              n2[l][t] = x_sum<B>(x < 7 ? nh64(n1[l][t], key) : n1[l][t]);
+          }
+          if (m == 64 && full) {
+#pragma unroll
+            for (int l = 0; l < 2; ++l)
+#pragma unroll
+              for (int t = 0; t < k; ++t) root[l][t] = n2[l][t];
+          } else if (m == 64) {
+            // a complete level-2 node of an incomplete item: it lies in the
+            // last, incomplete group of level 2, so it is pending there
+            const uint64_t j = (2 * c + (uint64_t)h) - ((N >> 6) & ~7ull);
+#pragma unroll
+            for (int t = 0; t < k; ++t)
+              if (x == t)
+                pend[t] += nh64(n2[0][t], final_key<W, B>(P, t, 2, j, 2 * p)) +
+                           nh64(n2[1][t], final_key<W, B>(P, t, 2, j, 2 * p + 1));
+            anyp = true;
+          }
+        }
+        if (m < 64 && cnt == 8) {
+          // complete level-1 node of an incomplete sub-chunk: pending, slot x
+#pragma unroll
+          for (int t = 0; t < k; ++t)
+            pend[t] += nh64(n1[0][t], final_key<W, B>(P, t, 1, x, 2 * p)) +
+                       nh64(n1[1][t], final_key<W, B>(P, t, 1, x, 2 * p + 1));
+          anyp = true;
+        }
+      } else if (m == 64) {
         // level 2 across the eight x-threads
         uint64_t n2[2][k];
 #pragma unroll
@@ -450,13 +511,17 @@ __device__ __forceinline__ uint64_t next_goff(const StrPlan &sp, int lvl, uint64
 // its final position is not known yet).  Otherwise its contribution to its
 // parent, NH under the tree key of its position (the eighth child enters
 // unhashed), is added into the group's accumulator.
-// Returns the group's slot, or kNoNode for a pending root.
-template <int W, bool INC>
+// Returns the group's slot, or kNoNode for a pending root.  With 256-bit
+// blocks (B = 4) both half-warps hold the same node above the work item;
+// the first half carries it.
+template <int W, bool INC, int B = kLanes>
 __device__ __forceinline__ uint64_t add_node(const KParams &P, const StrPlan &sp, int lvl, uint64_t idx,
                                              uint64_t goff, uint64_t v0, uint64_t v1, int ln,
                                              uint64_t (&pend)[Spec<W>::k], bool &anyp) {
+  static_assert(!INC || B == 8, "incremental updates use 512-bit blocks");
   constexpr int k = Spec<W>::k;
-  const int x = ln >> 2, p = ln & 3;
+  const int x = lane_x<B>(ln), p = lane_p<B>(ln);
+  const bool own = lane_h<B>(ln) == 0;
   const uint64_t C = sp.n_exec >> (3 * lvl);
   const uint64_t first_pending = C & ~7ull;
   if (idx >= first_pending) {
@@ -470,17 +535,17 @@ __device__ __forceinline__ uint64_t add_node(const KParams &P, const StrPlan &sp
     } else {
 #pragma unroll
       for (int t = 0; t < k; ++t)
-        if (x == t)
-          pend[t] += nh64(v0, final_key<W>(P, t, lvl, j, 2 * p)) +
-                     nh64(v1, final_key<W>(P, t, lvl, j, 2 * p + 1));
+        if (x == t && own)
+          pend[t] += nh64(v0, final_key<W, B>(P, t, lvl, j, 2 * p)) +
+                     nh64(v1, final_key<W, B>(P, t, lvl, j, 2 * p + 1));
       anyp = true;
     }
     return kNoNode;
   }
   const int pos = (int)(idx & 7);
   const uint64_t slot = sp.grp0 + goff + ((idx >> 3) - group_base<INC>(sp, lvl));
-  if (x < k) {
-    unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
+  if (x < k && own) {
+    unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * B + 2 * p;
     uint64_t a0 = v0, a1 = v1;
     if (pos < 7) {
       const uint64_t key = tree_key<W>(P, x, lvl, pos);
@@ -506,17 +571,28 @@ __device__ __forceinline__ unsigned arrive(const KParams &P, uint64_t slot, int 
 
 // The warp that made the eighth arrival takes the group's node (its
 // accumulator, then cleared for the next launch) into (v0, v1).
-template <int W>
+template <int W, int B = kLanes>
 __device__ __forceinline__ void take_group(const KParams &P, uint64_t slot, int ln, uint64_t &v0, uint64_t &v1) {
   constexpr int k = Spec<W>::k;
-  const int x = ln >> 2, p = ln & 3;
+  const int x = lane_x<B>(ln), p = lane_p<B>(ln);
   __threadfence();
   if (x < k) {
-    unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
+    unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * B + 2 * p;
     v0 = ld_cg(acc);
     v1 = ld_cg(acc + 1);
-    acc[0] = 0;
-    acc[1] = 0;
+    if (B == 8) {
+      acc[0] = 0;
+      acc[1] = 0;
+    }
+  }
+  if (B == 4) {
+    // both halves have read the node; the first clears it
+    __syncwarp();
+    if (x < k && lane_h<B>(ln) == 0) {
+      unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * B + 2 * p;
+      acc[0] = 0;
+      acc[1] = 0;
+    }
   }
   if (ln == 0) P.scr.grp_cnt[slot] = 0;
 }
@@ -524,17 +600,74 @@ __device__ __forceinline__ void take_group(const KParams &P, uint64_t slot, int 
 // Carries node idx of level lvl up the tree, waiting at every level: as long
 // as this warp's arrival completes a group, it takes the parent node and goes
 // on one level up.
-template <int W, bool INC>
+template <int W, bool INC, int B = kLanes>
 __device__ void climb(const KParams &P, const StrPlan &sp, int lvl, uint64_t idx, uint64_t goff,
                       uint64_t v0, uint64_t v1, int ln, uint64_t (&pend)[Spec<W>::k], bool &anyp) {
   for (;;) {
-    const uint64_t slot = add_node<W, INC>(P, sp, lvl, idx, goff, v0, v1, ln, pend, anyp);
+    const uint64_t slot = add_node<W, INC, B>(P, sp, lvl, idx, goff, v0, v1, ln, pend, anyp);
     if (slot == kNoNode) return;
     if (arrive(P, slot, ln) != kFan) return;
-    take_group<W>(P, slot, ln, v0, v1);
+    take_group<W, B>(P, slot, ln, v0, v1);
     goff = next_goff<INC>(sp, lvl, goff);
     lvl += 1;
     idx >>= 3;
+  }
+}
+
+// 256-bit blocks: the two level-2 nodes 2c and 2c+1 of a full work item c
+// (one per half-warp) enter their common level-3 group as one arrival of two
+// children -- each half adds the NH term of its own position, the first half
+// adds the sum -- or, in the last, incomplete group, are pending roots.
+// Returns the group's slot, or kNoNode.
+template <int W>
+__device__ __forceinline__ uint64_t add_pair(const KParams &P, const StrPlan &sp, uint64_t c,
+                                             uint64_t v0, uint64_t v1, int ln,
+                                             uint64_t (&pend)[Spec<W>::k], bool &anyp) {
+  constexpr int k = Spec<W>::k, B = 4, lvl = 2;
+  const int x = lane_x<B>(ln), p = lane_p<B>(ln), h = lane_h<B>(ln);
+  const uint64_t idx0 = 2 * c, idx = idx0 + (uint64_t)h;
+  const uint64_t first_pending = (sp.n_exec >> (3 * lvl)) & ~7ull;
+  if (idx0 >= first_pending) {  // (idx0 and idx0 + 1 share a group)
+    const uint64_t j = idx - first_pending;
+#pragma unroll
+    for (int t = 0; t < k; ++t)
+      if (x == t)
+        pend[t] += nh64(v0, final_key<W, B>(P, t, lvl, j, 2 * p)) +
+                   nh64(v1, final_key<W, B>(P, t, lvl, j, 2 * p + 1));
+    anyp = true;
+    return kNoNode;
+  }
+  const int pos = (int)(idx & 7);
+  const uint64_t slot = sp.grp0 + (idx0 >> 3);
+  uint64_t a0 = v0, a1 = v1;
+  if (x < k && pos < 7) {
+    const uint64_t key = tree_key<W>(P, x, lvl, pos);
+    a0 = nh64(v0, key);
+    a1 = nh64(v1, key);
+  }
+  a0 += __shfl_xor_sync(kFull, a0, 16);
+  a1 += __shfl_xor_sync(kFull, a1, 16);
+  if (x < k && h == 0) {
+    unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * B + 2 * p;
+    atomicAdd(acc, (unsigned long long)a0);
+    atomicAdd(acc + 1, (unsigned long long)a1);
+  }
+  return slot;
+}
+
+// The root(s) of full work item c enter the tree above the item and climb.
+template <int W, int L, int B>
+__device__ __forceinline__ void climb_item(const KParams &P, const StrPlan &sp, uint64_t c, uint64_t v0,
+                                           uint64_t v1, int ln, uint64_t (&pend)[Spec<W>::k], bool &anyp) {
+  if constexpr (B == 8) {
+    climb<W, false>(P, sp, L, c, 0, v0, v1, ln, pend, anyp);
+  } else {
+    static_assert(L == 2, "256-bit blocks take 64-execution sub-chunks");
+    const uint64_t slot = add_pair<W>(P, sp, c, v0, v1, ln, pend, anyp);
+    if (slot == kNoNode) return;
+    if (arrive(P, slot, ln, 2) != kFan) return;
+    take_group<W, B>(P, slot, ln, v0, v1);
+    climb<W, false, B>(P, sp, L + 1, (2 * c) >> 3, next_goff<false>(sp, L, 0), v0, v1, ln, pend, anyp);
   }
 }
 
@@ -555,7 +688,7 @@ __device__ __forceinline__ void flush_pending(const KParams &P, unsigned sidx, u
 
 // One chunk of a batch: its levels, the climb, and the string's completion
 // count (the warp that completes the string runs the finaliser).
-template <int W, int L, bool ALIGNED>
+template <int W, int L, bool ALIGNED, int B = kLanes>
 __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, uint64_t c, int ln) {
   constexpr int k = Spec<W>::k;
   uint64_t pend[k];  // this thread's share of the final-NH sum
@@ -563,12 +696,12 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, u
   for (int t = 0; t < k; ++t) pend[t] = 0;
   bool anyp = false;
   uint64_t v0, v1;
-  const bool full = chunk_root<W, L, ALIGNED>(P, sp, sp.ptr, c, ln, pend, anyp, v0, v1);
+  const bool full = chunk_root<W, L, ALIGNED, B>(P, sp, sp.ptr, c, ln, pend, anyp, v0, v1);
   griddep_wait();
-  if (full) climb<W, false>(P, sp, L, c, 0, v0, v1, ln, pend, anyp);
+  if (full) climb_item<W, L, B>(P, sp, c, v0, v1, ln, pend, anyp);
   if (sp.n_items == 1) {
     // (a single chunk's root is a pending root: the climb touched no scratch)
-    finish_local<W>(P, sp, sidx, pend, ln);
+    finish_local<W, B>(P, sp, sidx, pend, ln);
     return;
   }
   flush_pending<W>(P, sidx, pend, anyp, ln);
@@ -577,7 +710,7 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, u
   unsigned old = 0;
   if (ln == 0) old = atomicAdd(P.scr.str_done + sidx, 1u);
   old = __shfl_sync(kFull, old, 0);
-  if (old == sp.n_items - 1) finish_string<W>(P, sp, sidx, ln);
+  if (old == sp.n_items - 1) finish_string<W, B>(P, sp, sidx, ln);
 }
 
 // Incremental update, one warp: the stack carries, for every level, the
@@ -639,8 +772,9 @@ __device__ void seed_frontier(const KParams &P, const StrPlan &sp, int ln) {
 // that ends the string runs the finaliser.  An incremental update may take
 // its first chunk from the buffer of bytes carried over from earlier updates
 // (P.inc_first), and its first warp seeds the frontier groups.
-template <int W, int L, bool ALIGNED, bool INC>
+template <int W, int L, bool ALIGNED, bool INC, int B = kLanes>
 __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int ln) {
+  static_assert(!INC || B == 8, "incremental updates use 512-bit blocks");
   constexpr int k = Spec<W>::k;
   constexpr uint64_t G = (1ull << (3 * L)) * Dims<W>::exec_bytes;
   const StrPlan &sp = P.single;
@@ -666,11 +800,14 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
     if constexpr (INC) {
       if (P.inc_first && item == sp.chunk0) base = P.inc_first - item * G;
     }
-    const bool full = chunk_root<W, L, ALIGNED>(P, sp, base, item, ln, pend, anyp, v0, v1);
+    const bool full = chunk_root<W, L, ALIGNED, B>(P, sp, base, item, ln, pend, anyp, v0, v1);
     // everything below touches the scratch: an overlapping launch must first
     // see its predecessor finish
     griddep_wait();
-    if (full) climb<W, INC>(P, sp, L, item, 0, v0, v1, ln, pend, anyp);
+    if (full) {
+      if constexpr (INC) climb<W, INC>(P, sp, L, item, 0, v0, v1, ln, pend, anyp);
+      else climb_item<W, L, B>(P, sp, item, v0, v1, ln, pend, anyp);
+    }
     flush_pending<W>(P, 0, pend, anyp, ln);
   }
   griddep_wait();
@@ -730,19 +867,20 @@ __device__ __forceinline__ bool exit_protocol(const KParams &P, int ln) {
   return __shfl_sync(kFull, old, 0) == P.total_warps - 1;
 }
 
-template <int W, int L, bool SINGLE, bool ALIGNED, bool INC = false>
+// B: words per block, 8 (the default, 512-bit blocks) or 4 (256-bit blocks).
+template <int W, int L, bool SINGLE, bool ALIGNED, bool INC = false, int B = kLanes>
 __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KParams P) {
   static_assert(!INC || (SINGLE && L == 2), "incremental updates hash one string in 64-execution chunks");
   const int ln = threadIdx.x & 31;
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if constexpr (SINGLE) {
     griddep_launch_dependents();
-    single_string<W, L, ALIGNED, INC>(P, gw, ln);
+    single_string<W, L, ALIGNED, INC, B>(P, gw, ln);
     const bool last = exit_protocol(P, ln);
     // nothing is final in an incremental update; a string hashed over several
     // launches ends with the launch that reaches its item count (parts of a
     // split string set an unreachable count: they are finished elsewhere)
-    if (!INC && last && P.item_end >= P.single.n_items) finish_string<W>(P, P.single, 0, ln);
+    if (!INC && last && P.item_end >= P.single.n_items) finish_string<W, B>(P, P.single, 0, ln);
     return;
   } else {
     // a batch runs an aligned-only and a general variant; the planner's
@@ -761,9 +899,9 @@ __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KP
       const StrPlan sp = P.plans[s];
       const uint64_t c = item - sp.item0;
       if (ALIGNED || (((uintptr_t)sp.ptr) & 15u) == 0)
-        hash_chunk<W, L, true>(P, sp, s, c, ln);
+        hash_chunk<W, L, true, B>(P, sp, s, c, ln);
       else
-        hash_chunk<W, L, false>(P, sp, s, c, ln);
+        hash_chunk<W, L, false, B>(P, sp, s, c, ln);
     }
     exit_protocol(P, ln);
   }
@@ -900,10 +1038,11 @@ __global__ void __launch_bounds__(1024) plan_kernel(const PlanArgs A) {
 // loads: it computes the plans that the one-block planner above computes,
 // less the hybrid kernel's work list.
 
-template <int L>
+template <int L, int B = kLanes>
 __device__ __forceinline__ unsigned long long plan_items(uint64_t N) {
   if (L == 0) return ((N + 7) >> 3) + 1;
-  const uint64_t it = (N + (1ull << (3 * L)) - 1) >> (3 * L);
+  constexpr uint64_t CH = (uint64_t)(8 / B) << (3 * L);  // executions per item
+  const uint64_t it = (N + CH - 1) / CH;
   return it ? it : 1ull;
 }
 template <int L>
@@ -915,16 +1054,16 @@ __device__ __forceinline__ unsigned long long plan_groups(uint64_t N) {
 
 // 1: the work items and tree-group slots of every string of a tile, the
 // tile's totals and whether it holds a string that is not 16-byte aligned.
-template <int W, int L>
+template <int W, int L, int B = kLanes>
 __global__ void __launch_bounds__(1024) plan_tiles_kernel(const PlanArgs A) {
-  constexpr uint64_t B = Dims<W>::exec_bytes;
+  constexpr uint64_t XB = Dims<W, B>::exec_bytes;
   __shared__ unsigned long long sh[32];
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long it = 0, gr = 0;
   bool un = false;
   if (i < A.count) {
-    const uint64_t N = A.lens[i] / B;
-    it = plan_items<L>(N);
+    const uint64_t N = A.lens[i] / XB;
+    it = plan_items<L, B>(N);
     gr = plan_groups<L>(N);
     un = (((uintptr_t)A.ptrs[i]) & 15u) != 0;
   }
@@ -973,17 +1112,17 @@ __global__ void __launch_bounds__(1024) plan_totals_kernel(const PlanArgs A) {
 }
 
 // 3: every string's plan, its first item and its first group slot.
-template <int W, int L>
+template <int W, int L, int B = kLanes>
 __global__ void __launch_bounds__(1024) plan_write_kernel(const PlanArgs A) {
-  constexpr uint64_t B = Dims<W>::exec_bytes;
+  constexpr uint64_t XB = Dims<W, B>::exec_bytes;
   __shared__ unsigned long long sh[32];
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t len = 0, N = 0;
   unsigned long long it = 0, gr = 0;
   if (i < A.count) {
     len = A.lens[i];
-    N = len / B;
-    it = plan_items<L>(N);
+    N = len / XB;
+    it = plan_items<L, B>(N);
     gr = plan_groups<L>(N);
   }
   unsigned long long ti, tg;

@@ -1,0 +1,9 @@
+// Kernel instantiations for HalftimeHash40 with 256-bit blocks.
+#include "ht_kernels_v3.cuh"
+
+namespace ht {
+const KernelSet &kernels_w40_v3() {
+  static const KernelSet ks = make_kernel_set_v3<40>();
+  return ks;
+}
+}  // namespace ht

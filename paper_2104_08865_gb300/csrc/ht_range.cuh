@@ -282,6 +282,7 @@ KernelSet make_kernel_set() {
   ks.off_F = Dims<W>::off_F;
   ks.off_R = Dims<W>::off_R;
   ks.ew = Dims<W>::ew;
+  ks.lanes = kLanes;
   return ks;
 }
 

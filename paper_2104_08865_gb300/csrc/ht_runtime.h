@@ -65,7 +65,9 @@ namespace ht {
 int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what);
 const KernelSet *kernel_set(int width);
-uint64_t items_of(uint64_t N, int L);
+// Work items of a string of N executions for the warp-chunk kernel with
+// chunk height L and blocks of `lanes` words (8 or 4; at least one item).
+uint64_t items_of(uint64_t N, int L, int lanes = 8);
 uint64_t groups_of(uint64_t N, int L);
 // The next output of splitmix64 (Steele, Lea and Flood 2014) from *state.
 uint64_t splitmix64_next(uint64_t *state);

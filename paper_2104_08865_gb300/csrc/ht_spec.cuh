@@ -102,18 +102,22 @@ struct Spec<40> {
   }
 };
 
-// Derived sizes of a width.
-template <int W>
+// Derived sizes of a width with B words per block: B = 8 (512-bit blocks,
+// the paper's default) or B = 4 (256-bit blocks, the variant the paper labels
+// "v3" in Section 6.3).  B fixes the execution size and the sizes of the
+// final-NH and tail key regions.
+template <int W, int B = kLanes>
 struct Dims {
+  static_assert(B == 8 || B == 4, "blocks of 8 or 4 words");
   static constexpr int d = Spec<W>::d, e = Spec<W>::e, k = Spec<W>::k;
   static constexpr int dw = d * kItemWords;              // data words per lane
   static constexpr int ew = e * kItemWords;              // seed words of E
-  static constexpr int exec_bytes = 8 * kLanes * dw;     // one EHC execution
+  static constexpr int exec_bytes = 8 * B * dw;          // one EHC execution
   // seed regions, in words
   static constexpr int off_T = ew;
   static constexpr int off_F = off_T + k * kLevels * (kFan - 1);
-  static constexpr int off_R = off_F + k * kLevels * kFan * kLanes;
-  static constexpr int n_seed = off_R + kLanes * dw + k;
+  static constexpr int off_R = off_F + k * kLevels * kFan * B;
+  static constexpr int n_seed = off_R + B * dw + k;
 };
 
 }  // namespace ht

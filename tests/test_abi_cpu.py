@@ -46,6 +46,26 @@ def test_seed_expansion_matches_oracle(built, width):
         assert np.array_equal(abi.ht_seed_expand(s, width), oracle.seed_expand(s, oracle.seed_words(width)))
 
 
+@pytest.mark.parametrize("width", [16, 24, 32, 40])
+def test_seed_expansion_256_bit_blocks_matches_oracle(built, width):
+    from paper_2104_08865_gb300 import abi
+    code = width | abi.HT_BLOCK_256
+    assert abi.ht_seed_words(code) == oracle.seed_words(width, 4)
+    assert np.array_equal(abi.ht_seed_expand(7, code), oracle.seed_expand(7, oracle.seed_words(width, 4)))
+
+
+def test_256_bit_blocks_rejected_where_unsupported(built):
+    """The allocation-free call takes 8-word blocks only; it refuses the
+    256-bit-block code before any CUDA work.  Unknown flag bits are refused."""
+    from paper_2104_08865_gb300 import abi
+    code = 24 | abi.HT_BLOCK_256
+    with pytest.raises(abi.HalftimeError) as e:
+        abi.ht_hash_noalloc(code, abi.ht_seed_expand(7, code), 0, 0, 0)
+    assert e.value.code == abi.HT_ERR_WIDTH
+    assert abi.ht_seed_words(24 | 0x200) == 0
+    assert abi.ht_seed_words(abi.HT_BLOCK_256) == 0
+
+
 def test_argument_errors(built):
     from paper_2104_08865_gb300 import abi
     assert abi.ht_seed_words(17) == 0

@@ -511,3 +511,130 @@ def test_close_pairs_do_not_collide():
         a = oracle.hash_bytes(width, seeds, x)
         b = oracle.hash_bytes(width, seeds, y)
         assert not np.any(a == b), (i, wpos)
+
+
+# ------------------------------------------- 256-bit blocks (b = 4, "v3")
+
+@pytest.mark.parametrize("width", oracle.WIDTHS)
+def test_b4_block_layout_and_lanes(width):
+    """With blocks of 4 words, word (blk, lane) of an execution sits at byte
+    8*(blk*4 + lane) (Section 2): the probe of the 8-word layout test, at the
+    4-word stride, recovers 5*T[:, i] in its own lane only."""
+    p = oracle.params(width, 4)
+    T = _golden_matrices()[width]["T"]
+    for i in range(p["d"]):
+        for u in range(p["w"]):
+            for lane in range(4):
+                ex = np.zeros(p["exec_bytes"] // 8, dtype="<u8")
+                ex[(i * p["w"] + u) * 4 + lane] = 5
+                seeds = np.zeros(oracle.seed_words(width, 4), dtype=np.uint64)
+                seeds[i * p["w"] + u] = 1 << 32
+                y = oracle.ehc(width, seeds, ex.view(np.uint8), lane=lane, b=4)
+                assert [int(v) for v in y] == [5 * T[t][i] for t in range(p["k"])]
+                y2 = oracle.ehc(width, seeds, ex.view(np.uint8), lane=(lane + 1) % 4, b=4)
+                assert [int(v) for v in y2] == [0] * p["k"]
+
+
+@pytest.mark.parametrize("width", oracle.WIDTHS)
+def test_b4_lane_equals_b8_lane_on_restrided_words(width):
+    """EHC works per lane: lane j < 4 of a 4-word-block execution equals
+    lane j of the 8-word-block execution whose blocks hold the same words in
+    lanes 0..3 (and anything in lanes 4..7)."""
+    p4, p8 = oracle.params(width, 4), oracle.params(width, 8)
+    seeds = _seeds(width)
+    rng = np.random.default_rng(width)
+    for _ in range(4):
+        x4 = rng.integers(0, 2**64, p4["exec_bytes"] // 8, dtype=np.uint64)
+        x8 = rng.integers(0, 2**64, p8["exec_bytes"] // 8, dtype=np.uint64)
+        blocks = p4["d"] * p4["w"]
+        x8.reshape(blocks, 8)[:, :4] = x4.reshape(blocks, 4)
+        for lane in range(4):
+            a = oracle.ehc(width, seeds, x4.view(np.uint8), lane=lane, b=4)
+            b = oracle.ehc(width, seeds, x8.view(np.uint8), lane=lane, b=8)
+            assert np.array_equal(a, b), (width, lane)
+
+
+def test_b4_seed_layout():
+    """Seed regions with 4-word blocks: E = e*w, T = k*19*7, F = k*19*8*4,
+    R = 4*d*w + k (the layout of Section 6.2's budget at b = 4)."""
+    for width in oracle.WIDTHS:
+        assert oracle.seed_words(width, 4) == _layout(width, 4)["total"]
+    assert [oracle.seed_words(w, 4) for w in oracle.WIDTHS] == [1577, 2337, 3082, 3797]
+
+
+@pytest.mark.parametrize("width", oracle.WIDTHS)
+def test_b4_streaming_equals_recursive_twin(width):
+    p = oracle.params(width, 4)
+    xb = p["exec_bytes"]
+    seeds = _seeds(width, 7, 4)
+    Ns = [0, 1, 7, 8, 63, 64, 65, 127, 128, 129, 511, 512, 513, 585, 1100]
+    data = inputs.stream_bytes(14, 0, max(Ns) * xb + xb)
+    for N in Ns:
+        n = N * xb + (N * 37) % xb
+        a = oracle.hash_bytes(width, seeds, data[:n], b=4)
+        r = oracle.hash_bytes(width, seeds, data[:n], b=4, recursive=True)
+        assert np.array_equal(a, r), (width, N)
+
+
+def _tree_node(children, keys):
+    """Section 3.2 node variant at fan-out 8: NH of the first seven children
+    under the level's keys plus the eighth child."""
+    acc = children[7]
+    for i in range(7):
+        acc += _nh(children[i], keys[i])
+    return acc & M64
+
+
+def _complete_tree(leaves, level, tkeys):
+    """A complete 8-ary tree over 8^level leaves (node keys by height)."""
+    if level == 0:
+        return leaves[0]
+    span = 8 ** (level - 1)
+    kids = [_complete_tree(leaves[i * span:(i + 1) * span], level - 1, tkeys) for i in range(8)]
+    return _tree_node(kids, tkeys[level - 1])
+
+
+@pytest.mark.parametrize("width", [16, 24, 40])
+def test_b4_python_evaluation(width):
+    """The whole hash with 4-word blocks evaluated in Python integers from the
+    oracle's EHC leaves only: complete 8-ary trees taken from the front of the
+    leaf sequence, one per unit of each base-8 digit of N, highest level first
+    (Eq. stack-construction with fan-out 8); final NH of root j of level l in
+    lane i under F[t][l][j][i]; Toeplitz tail with the length word
+    (Section 6.1)."""
+    b = 4
+    p = oracle.params(width, b)
+    xb, k = p["exec_bytes"], p["k"]
+    seeds = _seeds(width, 31, b)
+    S = [int(x) for x in seeds]
+    L = _layout(width, b)
+    data_all = inputs.stream_bytes(15, 0, 600 * xb + xb)
+    for N in [0, 3, 8, 64, 71, 130, 519, 600]:
+        n = N * xb + (N * 53 + 11) % xb
+        data = data_all[:n]
+        leaves = [[oracle.ehc(width, seeds, data[x * xb:(x + 1) * xb], lane=i, b=b)
+                   for i in range(b)] for x in range(N)]
+        want = []
+        for t in range(k):
+            tkeys = [[S[L["T"] + (t * LEVELS + lv) * 7 + i] for i in range(7)] for lv in range(LEVELS)]
+            acc = 0
+            pos = 0
+            for lvl in range(LEVELS - 1, -1, -1):
+                span = 8 ** lvl
+                j = 0
+                while N - pos >= span:
+                    for i in range(b):
+                        ys = [int(leaves[x][i][t]) for x in range(pos, pos + span)]
+                        root = _complete_tree(ys, lvl, tkeys)
+                        fi = L["F"] + ((t * LEVELS + lvl) * 8 + j) * b + i
+                        acc = (acc + _nh(root, S[fi])) & M64
+                    pos += span
+                    j += 1
+            tail = bytes(data[N * xb:])
+            words = [int.from_bytes(tail[i:i + 8].ljust(8, b"\0"), "little")
+                     for i in range(0, len(tail), 8)] + [n]
+            for m, wd in enumerate(words):
+                acc = (acc + _nh(wd, S[L["R"] + t + m])) & M64
+            want.append(acc)
+        got = oracle.hash_bytes(width, seeds, data, b=b)
+        assert [int(v) for v in got] == want, (width, N)
