@@ -129,8 +129,31 @@ int ht_ctx_reserve(ht_ctx *ctx, uint64_t max_total_bytes, size_t max_strings);
 /* Waits for `stream`, then reads and clears the context's device status
  * word.  Returns HT_OK, or HT_ERR_TOO_LONG when a batch planned on the
  * device exceeded the reserved scratch (that batch's digests were not
- * written), or HT_ERR_CUDA. */
+ * written), HT_ERR_DEVICE when a bounded wait ran out or when the checked
+ * build skipped an out-of-range access (the message names the buffer and
+ * the index), or HT_ERR_CUDA. */
 int ht_ctx_status(ht_ctx *ctx, ht_stream_t stream);
+
+/* ---- checked build ----------------------------------------------------------
+ * The same sources compiled with -DHT_CHECK give libhalftime_check.so, a
+ * debug library with the same entry points in which every global-memory
+ * access of the warp-chunk kernels (single strings, batches, incremental
+ * updates, both block sizes) is first checked against the extent of its
+ * buffer (input string, seed region, tree-group scratch, per-string scratch,
+ * digests, incremental stack).  An out-of-range index is never accessed: the
+ * first one is recorded with its kind, the access is skipped (the digest is
+ * then wrong), and ht_ctx_status / ht_inc_status report HT_ERR_DEVICE.  It
+ * stands in for a memory checker where none can run; it is slower and is
+ * not the product library. */
+#define HT_BUILD_CHECKED 1u
+/* Build flags of the loaded library: HT_BUILD_CHECKED for the checked build. */
+unsigned ht_build_flags(void);
+/* Runs the checked build's range check once on the device, on `index`
+ * against `limit`, with no memory access at `index` (one thread; it tests
+ * the recorder, not a kernel): with index >= limit, ht_ctx_status then
+ * reports HT_ERR_DEVICE naming `index`.  In the normal build it does
+ * nothing.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_check_probe(ht_ctx *ctx, uint64_t index, uint64_t limit, ht_stream_t stream);
 
 /* ---- hashing ----------------------------------------------------------------
  * H(s, x) as in Section 5: generalized EHC over every 8*d*w-word execution
@@ -285,6 +308,12 @@ int ht_inc_update_host(ht_inc *h, const void *data_host, uint64_t len, ht_stream
 /* Writes the k digest words of the string to digest_dev (device) and closes
  * it (ht_inc_init opens the next one).  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
 int ht_inc_final(ht_inc *h, uint64_t *digest_dev, ht_stream_t stream);
+
+/* Waits for `stream`, then reads and clears the handle's device status word
+ * (its launches' own control block).  Returns HT_OK, or HT_ERR_DEVICE when
+ * the checked build skipped an out-of-range access in one of the handle's
+ * launches (see ht_build_flags), or HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_inc_status(ht_inc *h, ht_stream_t stream);
 
 /* Bytes appended so far to the open string. */
 uint64_t ht_inc_length(const ht_inc *h);

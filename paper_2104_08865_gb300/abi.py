@@ -14,7 +14,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhalftime.so")
+# HALFTIME_CHECKED=1 loads the checked build (every kernel access
+# range-checked; same entry points) instead of the product library
+CHECKED = os.environ.get("HALFTIME_CHECKED", "") == "1"
+LIB_PATH = os.path.join(_HERE, "libhalftime_check.so" if CHECKED else "libhalftime.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libhalftime.so is not built: run `python -c \"import __graft_entry__ as g; "
@@ -35,6 +38,7 @@ HT_ERR_DEVICE = -9
 WIDTHS = (16, 24, 32, 40)
 # width_bytes | HT_BLOCK_256 selects blocks of 4 words (256 bits) instead of 8
 HT_BLOCK_256 = 0x100
+HT_BUILD_CHECKED = 1
 
 
 class HalftimeError(RuntimeError):
@@ -119,6 +123,9 @@ _PROTOS = {
     "ht_get_shape": (_int, [_vp, _u64, ctypes.POINTER(ht_shape)]),
     "ht_set_shape": (_int, [_vp, _u64, ctypes.POINTER(ht_shape)]),
     "ht_ctx_launches": (_u64, [_vp]),
+    "ht_build_flags": (ctypes.c_uint, []),
+    "ht_check_probe": (_int, [_vp, _u64, _u64, _vp]),
+    "ht_inc_status": (_int, [_vp, _vp]),
     "ht_server_create": (_int, [_vp, _u64, ctypes.POINTER(ht_server_opts), ctypes.POINTER(_vp)]),
     "ht_server_create_fake": (_int, [_int, _u64, ctypes.POINTER(ht_server_opts), _u64,
                                      ctypes.c_int64, ctypes.POINTER(_vp)]),
@@ -287,6 +294,10 @@ def ht_inc_final(h: int, digest_dev, stream=None) -> None:
     _check(_lib.ht_inc_final(h, _ptr(digest_dev), _stream(stream)))
 
 
+def ht_inc_status(h: int, stream=None) -> None:
+    _check(_lib.ht_inc_status(h, _stream(stream)))
+
+
 def ht_inc_length(h: int) -> int:
     return int(_lib.ht_inc_length(h))
 
@@ -418,6 +429,15 @@ def ht_set_shape(ctx: int, length: int, kernel: int = 0, chunk_levels: int = 2, 
 
 def ht_ctx_launches(ctx: int) -> int:
     return int(_lib.ht_ctx_launches(ctx))
+
+
+def ht_build_flags() -> int:
+    """HT_BUILD_CHECKED for the checked build, else 0."""
+    return int(_lib.ht_build_flags())
+
+
+def ht_check_probe(ctx: int, index: int, limit: int, stream=None) -> None:
+    _check(_lib.ht_check_probe(ctx, index, limit, _stream(stream)))
 
 
 def _opts(n_streams=0, max_batch=0, max_queue=0, max_wait_us=0, pinned_mode=0):

@@ -1,9 +1,11 @@
-"""Builds libhalftime.so in-tree with nvcc for sm_103a.
+"""Builds libhalftime.so and its checked twin in-tree with nvcc for sm_103a.
 
 Every translation unit under csrc/ compiles in parallel to an object under
-_build/, then nvcc links them (static CUDA runtime) into
-paper_2104_08865_gb300/libhalftime.so.  Rebuilds only when a source or
-header is newer than the library.
+_build/ (and, with -DHT_CHECK, under _build_check/), then nvcc links them
+(static CUDA runtime) into paper_2104_08865_gb300/libhalftime.so and
+libhalftime_check.so (the debug library whose kernels range-check every
+global access).  Rebuilds only when a source or header is newer than a
+library.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhalftime.so")
+BUILD_CHECK = os.path.join(PKG, "_build_check")
+LIB_CHECK = os.path.join(PKG, "libhalftime_check.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -40,29 +44,34 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not stale():
+    targets = [(lib, d, flags) for lib, d, flags in ((LIB, BUILD, []), (LIB_CHECK, BUILD_CHECK, ["-DHT_CHECK"]))
+               if force or stale(lib)]
+    if not targets:
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     procs = []
-    objs = []
-    for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        objs.append(obj)
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
-        if src.endswith(".cpp"):
-            cmd = [nvcc] + NVCC_FLAGS + ["-x", "c++", "-c", src, "-o", obj]
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    links = []
+    for lib, bdir, extra in targets:
+        os.makedirs(bdir, exist_ok=True)
+        objs = []
+        for src in sources():
+            obj = os.path.join(bdir, os.path.basename(src) + ".o")
+            objs.append(obj)
+            cmd = [nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
+            if src.endswith(".cpp"):
+                cmd = [nvcc] + NVCC_FLAGS + extra + ["-x", "c++", "-c", src, "-o", obj]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        links.append((lib, objs))
     failed = []
     for src, p in procs:
         out, _ = p.communicate()
@@ -73,9 +82,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join("%s:\n%s" % f for f in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + ".tmp.%d" % os.getpid()
-    subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"], check=True)
-    os.replace(tmp, LIB)
+    for lib, objs in links:
+        tmp = lib + ".tmp.%d" % os.getpid()
+        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"], check=True)
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -13,10 +13,20 @@
 
 #include "halftime.h"
 #include "ht_internal.h"
+#include "ht_check.cuh"
 #include "ht_runtime.h"
 #include "ht_spec.cuh"
 
 namespace ht {
+
+// One range check of the checked build on (index, limit), touching nothing at
+// index (a test of the recorder).
+__global__ void check_probe_kernel(Ctl *ctl, uint64_t index, uint64_t limit) {
+  KParams P;
+  P.scr.ctl = ctl;
+  (void)HT_IN_RANGE(P, kChkInput, index, limit);
+  (void)P;
+}
 
 // ---- errors ---------------------------------------------------------------------
 
@@ -84,6 +94,34 @@ uint64_t groups_of(uint64_t N, int L) {
 // height: sum over strings of groups_of(N_i, 1) <= total_exec * (1/64 + 1/512
 // + ...) < total_exec / 56.
 static uint64_t groups_bound(uint64_t total_exec) { return total_exec / 56 + 1024; }
+
+// Waits for the stream, then reads and clears a control block's status word
+// (and, after a skipped out-of-range access in the checked build, the
+// recorded kind and index).
+int read_status(Ctl *ctl, cudaStream_t s) {
+  HT_CUDA(cudaStreamSynchronize(s));
+  unsigned int st = 0;
+  HT_CUDA(cudaMemcpy(&st, &ctl->status, sizeof st, cudaMemcpyDeviceToHost));
+  if (!st) return HT_OK;
+  unsigned int kind = 0;
+  unsigned long long index = 0;
+  if (st & kStatusBounds) {
+    HT_CUDA(cudaMemcpy(&kind, &ctl->bad_kind, sizeof kind, cudaMemcpyDeviceToHost));
+    HT_CUDA(cudaMemcpy(&index, &ctl->bad_index, sizeof index, cudaMemcpyDeviceToHost));
+    HT_CUDA(cudaMemset(&ctl->bad_kind, 0, sizeof kind));
+    HT_CUDA(cudaMemset(&ctl->bad_index, 0, sizeof index));
+  }
+  HT_CUDA(cudaMemset(&ctl->status, 0, sizeof st));
+  if (st & kStatusBounds) {
+    static const char *const names[] = {"?", "input", "tree keys", "final-NH keys", "tail keys",
+                                        "tree-group slot", "string slot", "digest row", "stack slot"};
+    return set_error(HT_ERR_DEVICE, "checked build: an access outside its buffer was skipped (%s, index %llu)",
+                     names[kind < 9 ? kind : 0], index);
+  }
+  if (st & kStatusTooLong)
+    return set_error(HT_ERR_TOO_LONG, "a batch exceeded the reserved scratch (no digests written)");
+  return set_error(HT_ERR_DEVICE, "a kernel gave up waiting for a shared-memory stage (status %u)", st);
+}
 
 static int bucket_of(uint64_t len) {
   if (len == UINT64_MAX) return 64;
@@ -173,6 +211,7 @@ static Scratch scratch_view(const ht_ctx *c) {
   s.str_done = c->str_done;
   s.ctl = c->ctl;
   s.cap_groups = c->cap_groups;
+  s.cap_strings = c->cap_strings;
   return s;
 }
 
@@ -427,17 +466,7 @@ int ht_ctx_reserve(ht_ctx *c, uint64_t max_total_bytes, size_t max_strings) {
 
 int ht_ctx_status(ht_ctx *c, ht_stream_t stream) {
   if (!c) return set_error(HT_ERR_ARG, "ht_ctx_status: NULL context");
-  HT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-  unsigned int st = 0;
-  HT_CUDA(cudaMemcpy(&st, &c->ctl->status, sizeof st, cudaMemcpyDeviceToHost));
-  if (st) {
-    unsigned int zero = 0;
-    HT_CUDA(cudaMemcpy(&c->ctl->status, &zero, sizeof zero, cudaMemcpyHostToDevice));
-    if (st & kStatusTooLong)
-      return set_error(HT_ERR_TOO_LONG, "a batch exceeded the reserved scratch (no digests written)");
-    return set_error(HT_ERR_DEVICE, "a kernel gave up waiting for a shared-memory stage (status %u)", st);
-  }
-  return HT_OK;
+  return read_status(c->ctl, (cudaStream_t)stream);
 }
 
 int ht_hash(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest, ht_stream_t stream) {
@@ -701,6 +730,15 @@ int ht_set_shape(ht_ctx *c, uint64_t len, const ht_shape *shape) {
 }
 
 uint64_t ht_ctx_launches(ht_ctx *c) { return c ? c->launches.load() : 0; }
+
+unsigned ht_build_flags(void) { return kChecked ? HT_BUILD_CHECKED : 0u; }
+
+int ht_check_probe(ht_ctx *c, uint64_t index, uint64_t limit, ht_stream_t stream) {
+  if (!c) return set_error(HT_ERR_ARG, "ht_check_probe: NULL context");
+  check_probe_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(c->ctl, index, limit);
+  HT_CUDA(cudaGetLastError());
+  return HT_OK;
+}
 
 int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
   if (!c || len == UINT64_MAX) return set_error(HT_ERR_ARG, "ht_autotune: bad arguments");

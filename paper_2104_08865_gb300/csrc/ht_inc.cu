@@ -90,6 +90,7 @@ void inc_params(const ht_inc *h, KParams &P) {
   P.scr.str_done = h->str_done;
   P.scr.ctl = h->ctl;
   P.scr.cap_groups = h->cap_groups;
+  P.scr.cap_strings = 1;
   P.stack = h->stack[h->cur];
   P.stack_in = h->stack[h->cur];
   P.count = 1;
@@ -232,6 +233,11 @@ int ht_inc_init(ht_inc *h, ht_stream_t stream) {
 }
 
 uint64_t ht_inc_length(const ht_inc *h) { return h ? h->chunks * h->granule + h->fill : 0; }
+
+int ht_inc_status(ht_inc *h, ht_stream_t stream) {
+  if (!h) return set_error(HT_ERR_ARG, "ht_inc_status: NULL handle");
+  return read_status(h->ctl, (cudaStream_t)stream);
+}
 
 uint64_t ht_inc_granule(const ht_inc *h) { return h ? h->granule : 0; }
 

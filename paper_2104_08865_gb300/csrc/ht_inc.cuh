@@ -36,14 +36,19 @@ __global__ void __launch_bounds__(32) inc_stack_kernel(const __grid_constant__ K
   if (x < k) {
     for (int lvl = 2; lvl < kLevels; ++lvl) {
       const int d = (int)((N >> (3 * lvl)) & 7);
-      for (int j = 0; j < d; ++j)
+      for (int j = 0; j < d; ++j) {
+        const uint64_t o = (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
+        if (!HT_IN_RANGE(P, kChkStack, o + 1, (uint64_t)kLevels * kFan * k * kLanes)) continue;
+        (void)o;
         s += nh64(*stack_node(P, k, lvl, j, x, 2 * p), final_key<W>(P, x, lvl, j, 2 * p)) +
              nh64(*stack_node(P, k, lvl, j, x, 2 * p + 1), final_key<W>(P, x, lvl, j, 2 * p + 1));
+      }
     }
   }
   s += __shfl_xor_sync(kFull, s, 1);
   s += __shfl_xor_sync(kFull, s, 2);
-  if (x < k && p == 0) atomicAdd(P.scr.str_acc + x, (unsigned long long)s);
+  if (x < k && p == 0 && HT_IN_RANGE(P, kChkString, 0, P.scr.cap_strings))
+    atomicAdd(P.scr.str_acc + x, (unsigned long long)s);
 }
 
 }  // namespace ht

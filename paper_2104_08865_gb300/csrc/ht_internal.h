@@ -37,12 +37,14 @@ struct Ctl {
   unsigned long long chunks_a;  // hybrid kernel: phase-A work items (whole chunks)
   unsigned long long units_b;   // hybrid kernel: phase-B work items (single units)
   unsigned int exit;          // warps that have left the work loop
-  unsigned int status;        // 0 or kStatusTooLong
+  unsigned int status;        // 0 or kStatus* bits
   unsigned int unaligned;     // planner: some string of the batch is not 16-byte aligned
-  unsigned int pad;
+  unsigned int bad_kind;      // checked build: kind of the first out-of-range access (0: none)
+  unsigned long long bad_index;  // checked build: its index
 };
 constexpr unsigned int kStatusTooLong = 1;  // a batch exceeded the scratch
-// (kStatusTimeout = 2: a bounded wait on a stage's mbarrier ran out)
+// (kStatusTimeout = 2: a bounded wait on a stage's mbarrier ran out;
+//  kStatusBounds = 4: the checked build skipped an out-of-range access)
 
 // Device scratch of one context.
 struct Scratch {
@@ -52,6 +54,7 @@ struct Scratch {
   unsigned int *str_done;       // [cap_strings] finished items per string
   Ctl *ctl;
   uint64_t cap_groups;
+  uint64_t cap_strings;
 };
 
 // Kernel parameters (passed as a __grid_constant__ struct: the hash keys of

@@ -25,6 +25,7 @@
 // x = (lane >> 1) & 7, p = lane & 1.
 #pragma once
 
+#include "ht_check.cuh"
 #include "ht_internal.h"
 #include "ht_spec.cuh"
 
@@ -234,11 +235,15 @@ __device__ __forceinline__ void ehc2(const uint8_t *ex, int p, uint32_t sh,
 
 template <int W>
 __device__ __forceinline__ uint64_t tree_key(const KParams &P, int t, int lvl, int i) {
-  return __ldg(P.seeds + Dims<W>::off_T + (t * kLevels + lvl) * (kFan - 1) + i);
+  const int r = (t * kLevels + lvl) * (kFan - 1) + i;
+  if (!HT_IN_RANGE(P, kChkSeedT, r, Spec<W>::k * kLevels * (kFan - 1))) return 0;
+  return __ldg(P.seeds + Dims<W>::off_T + r);
 }
 template <int W, int B = kLanes>
 __device__ __forceinline__ uint64_t final_key(const KParams &P, int t, int lvl, uint64_t j, int lane) {
-  return __ldg(P.seeds + Dims<W, B>::off_F + ((t * kLevels + lvl) * kFan + (int)j) * B + lane);
+  const uint64_t r = ((uint64_t)(t * kLevels + lvl) * kFan + j) * B + lane;
+  if (!HT_IN_RANGE(P, kChkSeedF, r, Spec<W>::k * kLevels * kFan * B)) return 0;
+  return __ldg(P.seeds + Dims<W, B>::off_F + r);
 }
 
 // ---- the finaliser: pending-root sum + Toeplitz tail (Section 6.1) ----------
@@ -256,15 +261,19 @@ __device__ __forceinline__ void tail_sum(const KParams &P, const StrPlan &sp, in
 #pragma unroll
   for (int t = 0; t < k; ++t) sum[t] = 0;
   for (uint32_t m = ln; m <= M; m += 32) {
-    uint64_t word;
+    uint64_t word = 0;
     if (m == M) {
       word = sp.len;
     } else {
       const uint64_t rem = tlen - 8ull * m;
-      word = tail_word(sp.ptr + tstart + 8ull * m, rem < 8 ? (uint32_t)rem : 8u);
+      const uint32_t nb = rem < 8 ? (uint32_t)rem : 8u;
+      if (HT_IN_RANGE(P, kChkInput, tstart + 8ull * m + nb - 1, sp.len))
+        word = tail_word(sp.ptr + tstart + 8ull * m, nb);
     }
 #pragma unroll
-    for (int t = 0; t < k; ++t) sum[t] += nh64(word, __ldg(P.seeds + Dims<W, B>::off_R + t + m));
+    for (int t = 0; t < k; ++t)
+      if (HT_IN_RANGE(P, kChkSeedR, t + m, (B * Dims<W, B>::dw + k)))
+        sum[t] += nh64(word, __ldg(P.seeds + Dims<W, B>::off_R + t + m));
   }
 #pragma unroll
   for (int t = 0; t < k; ++t) sum[t] = warp_sum(sum[t]);
@@ -274,15 +283,17 @@ template <int W, int B = kLanes>
 __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx, int ln) {
   constexpr int k = Spec<W>::k;
   __threadfence();
+  const bool str_ok = HT_IN_RANGE(P, kChkString, sidx, P.scr.cap_strings);
   uint64_t acc[k];
 #pragma unroll
-  for (int t = 0; t < k; ++t) acc[t] = ld_cg(P.scr.str_acc + (uint64_t)sidx * k + t);
+  for (int t = 0; t < k; ++t) acc[t] = str_ok ? ld_cg(P.scr.str_acc + (uint64_t)sidx * k + t) : 0;
   uint64_t sum[k];
   tail_sum<W, B>(P, sp, ln, sum);
-  if (ln == 0) {
+  if (ln == 0 && str_ok) {
+    const bool dig_ok = HT_IN_RANGE(P, kChkDigest, sidx, P.count);
 #pragma unroll
     for (int t = 0; t < k; ++t) {
-      P.digests[(uint64_t)sidx * k + t] = acc[t] + sum[t];
+      if (dig_ok) P.digests[(uint64_t)sidx * k + t] = acc[t] + sum[t];
       P.scr.str_acc[(uint64_t)sidx * k + t] = 0;
     }
     P.scr.str_done[sidx] = 0;
@@ -300,7 +311,7 @@ __device__ void finish_local(const KParams &P, const StrPlan &sp, unsigned sidx,
   tail_sum<W, B>(P, sp, ln, sum);
 #pragma unroll
   for (int t = 0; t < k; ++t) sum[t] += warp_sum(pend[t]);
-  if (ln == 0)
+  if (ln == 0 && HT_IN_RANGE(P, kChkDigest, sidx, P.count))
 #pragma unroll
     for (int t = 0; t < k; ++t) P.digests[(uint64_t)sidx * k + t] = sum[t];
 }
@@ -342,7 +353,8 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
       // eight executions, one per x-thread; level 1 across the x-threads
       const int m = (int)((N - e0) < 8 ? (N - e0) : 8);
       uint64_t y[2][k];
-      if (x < m) ehc2<W, ALIGNED>(base + (e0 + (uint64_t)x) * XB, p, sh, P, y);
+      if (x < m && HT_IN_RANGE(P, kChkInput, (e0 + x + 1) * XB - 1, sp.len))
+        ehc2<W, ALIGNED>(base + (e0 + (uint64_t)x) * XB, p, sh, P, y);
       if (full) {
 #pragma unroll
         for (int t = 0; t < k; ++t) {
@@ -380,6 +392,7 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
 #pragma unroll 2
         for (int s = 0; s < 8; ++s) {
           uint64_t y[2][k];
+          if (kChecked && !HT_IN_RANGE(P, kChkInput, (sb + 8ull * x + s + 1) * XB - 1, sp.len)) continue;
           ehc2<W, ALIGNED, B>(ex + s * XB, p, sh, P, y);
 #pragma unroll
           for (int l = 0; l < 2; ++l)
@@ -392,6 +405,7 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
 #pragma unroll 1
         for (int s = 0; s < cnt; ++s) {
           uint64_t y[2][k];
+          if (kChecked && !HT_IN_RANGE(P, kChkInput, (sb + 8ull * x + s + 1) * XB - 1, sp.len)) continue;
           ehc2<W, ALIGNED, B>(ex + s * XB, p, sh, P, y);
 #pragma unroll
           for (int t = 0; t < k; ++t)
@@ -527,10 +541,10 @@ __device__ __forceinline__ uint64_t add_node(const KParams &P, const StrPlan &sp
   if (idx >= first_pending) {
     const uint64_t j = idx - first_pending;
     if constexpr (INC) {
-      if (x < k) {
-        unsigned long long *st = P.stack + (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
-        st[0] = v0;
-        st[1] = v1;
+      const uint64_t o = (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
+      if (x < k && HT_IN_RANGE(P, kChkStack, o + 1, (uint64_t)kLevels * kFan * k * kLanes)) {
+        P.stack[o] = v0;
+        P.stack[o + 1] = v1;
       }
     } else {
 #pragma unroll
@@ -544,7 +558,7 @@ __device__ __forceinline__ uint64_t add_node(const KParams &P, const StrPlan &sp
   }
   const int pos = (int)(idx & 7);
   const uint64_t slot = sp.grp0 + goff + ((idx >> 3) - group_base<INC>(sp, lvl));
-  if (x < k && own) {
+  if (x < k && own && HT_IN_RANGE(P, kChkGroup, slot, P.scr.cap_groups)) {
     unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * B + 2 * p;
     uint64_t a0 = v0, a1 = v1;
     if (pos < 7) {
@@ -565,7 +579,7 @@ __device__ __forceinline__ unsigned arrive(const KParams &P, uint64_t slot, int 
   __threadfence();
   __syncwarp();
   unsigned old = 0;
-  if (ln == 0) old = atomicAdd(P.scr.grp_cnt + slot, n);
+  if (ln == 0 && HT_IN_RANGE(P, kChkGroup, slot, P.scr.cap_groups)) old = atomicAdd(P.scr.grp_cnt + slot, n);
   return __shfl_sync(kFull, old, 0) + n;
 }
 
@@ -576,7 +590,8 @@ __device__ __forceinline__ void take_group(const KParams &P, uint64_t slot, int 
   constexpr int k = Spec<W>::k;
   const int x = lane_x<B>(ln), p = lane_p<B>(ln);
   __threadfence();
-  if (x < k) {
+  const bool ok = HT_IN_RANGE(P, kChkGroup, slot, P.scr.cap_groups);
+  if (x < k && ok) {
     unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * B + 2 * p;
     v0 = ld_cg(acc);
     v1 = ld_cg(acc + 1);
@@ -588,13 +603,13 @@ __device__ __forceinline__ void take_group(const KParams &P, uint64_t slot, int 
   if (B == 4) {
     // both halves have read the node; the first clears it
     __syncwarp();
-    if (x < k && lane_h<B>(ln) == 0) {
+    if (x < k && lane_h<B>(ln) == 0 && ok) {
       unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * B + 2 * p;
       acc[0] = 0;
       acc[1] = 0;
     }
   }
-  if (ln == 0) P.scr.grp_cnt[slot] = 0;
+  if (ln == 0 && ok) P.scr.grp_cnt[slot] = 0;
 }
 
 // Carries node idx of level lvl up the tree, waiting at every level: as long
@@ -647,7 +662,7 @@ __device__ __forceinline__ uint64_t add_pair(const KParams &P, const StrPlan &sp
   }
   a0 += __shfl_xor_sync(kFull, a0, 16);
   a1 += __shfl_xor_sync(kFull, a1, 16);
-  if (x < k && h == 0) {
+  if (x < k && h == 0 && HT_IN_RANGE(P, kChkGroup, slot, P.scr.cap_groups)) {
     unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * B + 2 * p;
     atomicAdd(acc, (unsigned long long)a0);
     atomicAdd(acc + 1, (unsigned long long)a1);
@@ -679,7 +694,7 @@ __device__ __forceinline__ void flush_pending(const KParams &P, unsigned sidx, u
   if (__any_sync(kFull, anyp)) {
 #pragma unroll
     for (int t = 0; t < k; ++t) pend[t] = warp_sum(pend[t]);
-    if (ln == 0)
+    if (ln == 0 && HT_IN_RANGE(P, kChkString, sidx, P.scr.cap_strings))
 #pragma unroll
       for (int t = 0; t < k; ++t)
         if (pend[t]) atomicAdd(P.scr.str_acc + (uint64_t)sidx * k + t, (unsigned long long)pend[t]);
@@ -708,7 +723,7 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, u
   __threadfence();
   __syncwarp();
   unsigned old = 0;
-  if (ln == 0) old = atomicAdd(P.scr.str_done + sidx, 1u);
+  if (ln == 0 && HT_IN_RANGE(P, kChkString, sidx, P.scr.cap_strings)) old = atomicAdd(P.scr.str_done + sidx, 1u);
   old = __shfl_sync(kFull, old, 0);
   if (old == sp.n_items - 1) finish_string<W, B>(P, sp, sidx, ln);
 }
@@ -736,6 +751,7 @@ __device__ void seed_frontier(const KParams &P, const StrPlan &sp, int ln) {
       if (x < k)
         for (unsigned j = 0; j < d; ++j) {
           const uint64_t o = (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
+          if (!HT_IN_RANGE(P, kChkStack, o + 1, (uint64_t)kLevels * kFan * k * kLanes)) continue;
           P.stack[o] = P.stack_in[o];
           P.stack[o + 1] = P.stack_in[o + 1];
         }
@@ -746,12 +762,15 @@ __device__ void seed_frontier(const KParams &P, const StrPlan &sp, int ln) {
         for (unsigned j = 0; j < d; ++j) {  // j < 7: every stack node is hashed
           const uint64_t key = tree_key<W>(P, x, lvl, (int)j);
           const uint64_t o = (((uint64_t)lvl * kFan + j) * k + (uint64_t)x) * kLanes + 2 * p;
+          if (!HT_IN_RANGE(P, kChkStack, o + 1, (uint64_t)kLevels * kFan * k * kLanes)) continue;
           a0 += nh64(P.stack_in[o], key);
           a1 += nh64(P.stack_in[o + 1], key);
         }
-        unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
-        atomicAdd(acc, (unsigned long long)a0);
-        atomicAdd(acc + 1, (unsigned long long)a1);
+        if (HT_IN_RANGE(P, kChkGroup, slot, P.scr.cap_groups)) {
+          unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
+          atomicAdd(acc, (unsigned long long)a0);
+          atomicAdd(acc + 1, (unsigned long long)a1);
+        }
       }
       if (arrive(P, slot, ln, d) == kFan) {
         uint64_t pend[k];  // (unused: incremental pending nodes go to the stack)

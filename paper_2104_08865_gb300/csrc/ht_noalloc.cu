@@ -122,6 +122,7 @@ extern "C" int ht_hash_noalloc(int width_bytes, const uint64_t *seed_words_host,
   P.scr.str_done = reinterpret_cast<unsigned int *>(base + kOffStrDone);
   P.scr.ctl = reinterpret_cast<ht::Ctl *>(base + kOffCtl);
   P.scr.cap_groups = max_groups;
+  P.scr.cap_strings = 1;
   ht::StrPlan &sp = P.single;
   sp.ptr = static_cast<const uint8_t *>(data_dev);
   sp.len = len;

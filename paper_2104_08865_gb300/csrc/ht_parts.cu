@@ -49,6 +49,7 @@ void part_params(const ht_ctx *c, ht::KParams &P, uint64_t total_len) {
   P.scr.grp_acc = b + 9 + L.cnt_words;
   P.scr.ctl = c->ctl;
   P.scr.cap_groups = L.groups;
+  P.scr.cap_strings = 1;
   ht::StrPlan &sp = P.single;
   sp.len = total_len;
   sp.n_exec = total_len / (uint64_t)ks.exec_bytes;

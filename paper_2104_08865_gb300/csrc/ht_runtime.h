@@ -73,4 +73,7 @@ uint64_t groups_of(uint64_t N, int L);
 uint64_t splitmix64_next(uint64_t *state);
 // Zeroes P, then fills the hash keys, the seed pointer and the context's scratch.
 void fill_keys(const ht_ctx *c, KParams &P);
+// Waits for the stream, then reads and clears a control block's status word;
+// returns HT_OK or the error it reports.
+int read_status(Ctl *ctl, cudaStream_t s);
 }  // namespace ht

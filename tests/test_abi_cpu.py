@@ -38,6 +38,18 @@ def test_library_exports_every_declared_symbol(built):
     assert set(abi.exported_symbols()) == declared
 
 
+def test_checked_build_exports_the_same_symbols(built):
+    """libhalftime_check.so (range-checked kernels) has every entry point and
+    says it is the checked build; the product library says it is not."""
+    from paper_2104_08865_gb300 import abi
+    lib = ctypes.CDLL(os.path.join(os.path.dirname(abi.LIB_PATH), "libhalftime_check.so"))
+    for name in sorted(_header_functions()):
+        assert hasattr(lib, name), name
+    lib.ht_build_flags.restype = ctypes.c_uint
+    assert lib.ht_build_flags() == abi.HT_BUILD_CHECKED
+    assert abi.ht_build_flags() == 0
+
+
 @pytest.mark.parametrize("width", [16, 24, 32, 40])
 def test_seed_expansion_matches_oracle(built, width):
     from paper_2104_08865_gb300 import abi
