@@ -134,6 +134,14 @@ int ht_ctx_reserve(ht_ctx *ctx, uint64_t max_total_bytes, size_t max_strings);
  * the index), or HT_ERR_CUDA. */
 int ht_ctx_status(ht_ctx *ctx, ht_stream_t stream);
 
+/* Runs, on `stream`, the bounded wait that the stream kernel uses for its
+ * shared-memory stages, on a stage that nothing fills, for `cycles` SM
+ * clock cycles (1 .. 2^34): the wait runs out, the kernel reports it in the
+ * context's status word and returns, and ht_ctx_status then gives
+ * HT_ERR_DEVICE; the context stays usable.  For testing the timeout path.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_wait_probe(ht_ctx *ctx, uint64_t cycles, ht_stream_t stream);
+
 /* ---- checked build ----------------------------------------------------------
  * The same sources compiled with -DHT_CHECK give libhalftime_check.so, a
  * debug library with the same entry points in which every global-memory

@@ -125,6 +125,7 @@ _PROTOS = {
     "ht_ctx_launches": (_u64, [_vp]),
     "ht_build_flags": (ctypes.c_uint, []),
     "ht_check_probe": (_int, [_vp, _u64, _u64, _vp]),
+    "ht_wait_probe": (_int, [_vp, _u64, _vp]),
     "ht_inc_status": (_int, [_vp, _vp]),
     "ht_server_create": (_int, [_vp, _u64, ctypes.POINTER(ht_server_opts), ctypes.POINTER(_vp)]),
     "ht_server_create_fake": (_int, [_int, _u64, ctypes.POINTER(ht_server_opts), _u64,
@@ -434,6 +435,10 @@ def ht_ctx_launches(ctx: int) -> int:
 def ht_build_flags() -> int:
     """HT_BUILD_CHECKED for the checked build, else 0."""
     return int(_lib.ht_build_flags())
+
+
+def ht_wait_probe(ctx: int, cycles: int, stream=None) -> None:
+    _check(_lib.ht_wait_probe(ctx, cycles, _stream(stream)))
 
 
 def ht_check_probe(ctx: int, index: int, limit: int, stream=None) -> None:

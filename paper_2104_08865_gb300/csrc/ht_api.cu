@@ -738,6 +738,15 @@ uint64_t ht_ctx_launches(ht_ctx *c) { return c ? c->launches.load() : 0; }
 
 unsigned ht_build_flags(void) { return kChecked ? HT_BUILD_CHECKED : 0u; }
 
+int ht_wait_probe(ht_ctx *c, uint64_t cycles, ht_stream_t stream) {
+  if (!c || cycles == 0 || cycles > (1ull << 34)) return set_error(HT_ERR_ARG, "ht_wait_probe: bad arguments");
+  Ctl *ctl = c->ctl;
+  long long budget = (long long)cycles;
+  void *args[] = {&ctl, &budget};
+  HT_CUDA(cudaLaunchKernel(c->ks->wait_probe, dim3(1), dim3(32), args, 0, (cudaStream_t)stream));
+  return HT_OK;
+}
+
 int ht_check_probe(ht_ctx *c, uint64_t index, uint64_t limit, ht_stream_t stream) {
   if (!c) return set_error(HT_ERR_ARG, "ht_check_probe: NULL context");
   check_probe_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(c->ctl, index, limit);

@@ -122,6 +122,7 @@ struct KernelSet {
   const void *inc_aligned;    // incremental: whole chunks of one update
   const void *inc_unaligned;
   const void *inc_stack;      // incremental: pending stack nodes into the sum
+  const void *wait_probe;     // a bounded wait that runs out (tests the timeout path)
   int exec_bytes, k, n_seed, off_T, off_F, off_R, ew;
   // words per block: 8, or 4 for the 256-bit-block variant, whose set holds
   // only the warp-chunk kernels with 64-execution sub-chunks (index L = 2)

@@ -4,7 +4,7 @@
 // multi-block batch planner.  One translation unit per width includes it.
 #pragma once
 
-#include "ht_kernel.cuh"
+#include "ht_stream.cuh"
 
 namespace ht {
 
@@ -19,6 +19,7 @@ inline KernelSet make_kernel_set_v3() {
   ks.plan_tiles[L] = (const void *)plan_tiles_kernel<W, L, B>;
   ks.plan_totals = (const void *)plan_totals_kernel<W>;
   ks.plan_write[L] = (const void *)plan_write_kernel<W, L, B>;
+  ks.wait_probe = (const void *)wait_probe_kernel<W>;
   ks.exec_bytes = Dims<W, B>::exec_bytes;
   ks.k = Spec<W>::k;
   ks.n_seed = Dims<W, B>::n_seed;

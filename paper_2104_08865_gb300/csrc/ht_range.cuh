@@ -275,6 +275,7 @@ KernelSet make_kernel_set() {
   ks.inc_aligned = (const void *)hash_kernel<W, 2, true, true, true>;
   ks.inc_unaligned = (const void *)hash_kernel<W, 2, true, false, true>;
   ks.inc_stack = (const void *)inc_stack_kernel<W>;
+  ks.wait_probe = (const void *)wait_probe_kernel<W>;
   ks.exec_bytes = Dims<W>::exec_bytes;
   ks.k = Spec<W>::k;
   ks.n_seed = Dims<W>::n_seed;

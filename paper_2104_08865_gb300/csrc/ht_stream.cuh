@@ -46,8 +46,8 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
       : "memory");
 }
 
-// Waits for the phase of `parity` to complete; false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Waits for the phase of `parity` to complete; false after `budget` cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget = kWaitCycles) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -57,7 +57,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > budget) return false;
   }
 }
 
@@ -429,6 +429,21 @@ __global__ void __launch_bounds__(256) stream_kernel(const __grid_constant__ KPa
       for (uint64_t sq = cseq; sq < pseq; ++sq) mbar_wait(bars + 8 * (unsigned)(sq % R), (uint32_t)((sq / R) & 1));
     __syncwarp();
   }
+}
+
+// A bounded wait that runs out, for testing the timeout path: one warp
+// waits, with mbar_wait, on a shared-memory mbarrier that nothing arrives on
+// and no copy completes, for `budget` cycles, then reports kStatusTimeout in
+// the status word like the stream kernel does and returns.  (W only gives
+// each width's table its own instance.)
+template <int W>
+__global__ void __launch_bounds__(32) wait_probe_kernel(Ctl *ctl, long long budget) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) mbar_init(b);
+  __syncwarp();
+  const bool ok = mbar_wait(b, 0, budget);
+  if (!ok && threadIdx.x == 0) atomicOr(&ctl->status, kStatusTimeout);
 }
 
 }  // namespace ht
