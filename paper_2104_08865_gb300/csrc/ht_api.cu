@@ -152,8 +152,11 @@ static void free_scratch(ht_ctx *c) {
   cudaFree(c->tile_items);
   cudaFree(c->tile_groups);
   cudaFree(c->tile_flags);
+  cudaFree(c->item_str);
   c->tile_items = c->tile_groups = nullptr;
   c->tile_flags = nullptr;
+  c->item_str = nullptr;
+  c->cap_items = 0;
   c->chunk0s = nullptr;
   c->unitb0s = nullptr;
   c->grp_acc = nullptr;
@@ -187,12 +190,18 @@ static int alloc_scratch(ht_ctx *c, uint64_t groups, uint64_t strings) {
   grab((void **)&c->tile_items, tiles * sizeof(unsigned long long));
   grab((void **)&c->tile_groups, tiles * sizeof(unsigned long long));
   grab((void **)&c->tile_flags, tiles * sizeof(unsigned int));
+  // the item -> string map of warp-chunk batches with 64-execution (or
+  // larger) items: a string of N executions has at most 1 + N/64 <=
+  // 9 + 8 groups_of(N) items, so any batch that fits the group slots fits
+  const uint64_t items = 8 * groups + 9 * strings;
+  grab((void **)&c->item_str, items * sizeof(unsigned int));
   if (e != cudaSuccess) {
     free_scratch(c);
     return cuda_error(e, "scratch allocation");
   }
   c->cap_groups = groups;
   c->cap_strings = strings;
+  c->cap_items = items;
   return HT_OK;
 }
 
@@ -565,10 +574,11 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
 // also lays out its two-phase work list.  Node parameters are replaced on
 // every call; the graph is rebuilt when the batch shape changes.
 struct BatchNodes {
-  cudaKernelNodeParams plan, totals, write, hash, hash2;
+  cudaKernelNodeParams plan, totals, write, items, hash, hash2;
   void *pargs[1], *hargs[1];
   bool multi;   // multi-block planner
   bool general; // a general (unaligned-capable) batch kernel follows the aligned-only one
+  bool map;     // the planner writes the item -> string map (warp-chunk kernel, L >= 2)
 };
 
 // The general (unaligned-capable) batch kernel paired with the aligned-only
@@ -582,6 +592,10 @@ static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
   const int pl = shape.kernel == 1 ? shape.chunk_levels : 0;
   n.multi = shape.kernel != 2;
   n.general = shape.kernel != 0;
+  n.map = shape.kernel == 1 && shape.chunk_levels >= 2;
+  c->plan_args.item_str = n.map ? c->item_str : nullptr;
+  c->plan_args.cap_items = n.map ? c->cap_items : 0;
+  c->batch_params.item_str = n.map ? c->item_str : nullptr;
   n.pargs[0] = &c->plan_args;
   const unsigned tiles = std::max(1u, (c->plan_args.count + 1023) / 1024);
   c->plan_args.n_tiles = tiles;
@@ -596,6 +610,10 @@ static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
     n.totals.gridDim = dim3(1);
     n.write = n.plan;
     n.write.func = (void *)ks.plan_write[pl];
+    n.items = n.plan;
+    n.items.func = (void *)ks.plan_items;
+    n.items.gridDim = dim3((unsigned)(2 * c->num_sms));
+    n.items.blockDim = dim3(256);
   } else {
     n.plan.func = (void *)ks.plan[pl];
     n.plan.gridDim = dim3(1);
@@ -631,7 +649,7 @@ static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
   c->graph = nullptr;
-  c->node_hash2 = c->node_totals = c->node_write = nullptr;
+  c->node_hash2 = c->node_totals = c->node_write = c->node_items = nullptr;
   BatchNodes n;
   batch_nodes(c, shape, n);
   HT_CUDA(cudaGraphCreate(&c->graph, 0));
@@ -642,6 +660,10 @@ static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
     last = c->node_totals;
     HT_CUDA(cudaGraphAddKernelNode(&c->node_write, c->graph, &last, 1, &n.write));
     last = c->node_write;
+    if (n.map) {
+      HT_CUDA(cudaGraphAddKernelNode(&c->node_items, c->graph, &last, 1, &n.items));
+      last = c->node_items;
+    }
   }
   HT_CUDA(cudaGraphAddKernelNode(&c->node_hash, c->graph, &last, 1, &n.hash));
   if (n.general) {
@@ -695,11 +717,12 @@ int ht_hash_batch(ht_ctx *c, const void *const *ptrs, const uint64_t *lens, size
     HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_plan, &n.plan));
     if (c->node_totals) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_totals, &n.totals));
     if (c->node_write) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_write, &n.write));
+    if (c->node_items) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_items, &n.items));
     HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash, &n.hash));
     if (c->node_hash2) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash2, &n.hash2));
   }
   HT_CUDA(cudaGraphLaunch(c->graph_exec, s));
-  c->launches.fetch_add(2 + (c->node_totals ? 2 : 0) + (c->node_hash2 ? 1 : 0));
+  c->launches.fetch_add(2 + (c->node_totals ? 2 : 0) + (c->node_items ? 1 : 0) + (c->node_hash2 ? 1 : 0));
   return HT_OK;
 }
 

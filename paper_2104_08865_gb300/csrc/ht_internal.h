@@ -68,6 +68,7 @@ struct KParams {
   const unsigned long long *item0s;  // batch mode: item0 of each string (+ total)
   const unsigned long long *chunk0s;  // batch mode: chunk0 of each string (+ total)
   const unsigned long long *unitb0s;  // batch mode: unitb0 of each string (+ total)
+  const unsigned int *item_str;  // batch mode: the string of every work item (or null: search item0s)
   unsigned long long *digests;  // count * k words
   unsigned long long *stack;    // incremental mode: pending nodes [level][8][k][8] (written)
   const unsigned long long *stack_in;  // incremental mode: the previous update's stack (read)
@@ -96,6 +97,10 @@ struct PlanArgs {
   unsigned long long *tile_groups;
   unsigned int *tile_flags;
   unsigned int n_tiles;
+  // warp-chunk batches: the string of every work item (capacity cap_items;
+  // 0 when the batch kernel searches item0s instead)
+  unsigned int *item_str;
+  uint64_t cap_items;
 };
 
 // Kernel variants of one width.  Warp-chunk kernels: chunk height L in
@@ -111,6 +116,7 @@ struct KernelSet {
   const void *plan_tiles[4];        // multi-block planner, same index: tile totals
   const void *plan_totals;          //   their prefix sums and the batch totals
   const void *plan_write[4];        //   every string's plan
+  const void *plan_items;           //   the string of every work item
   const void *stream_single;
   const void *stream_batch;
   const void *range_single;  // hybrid kernel: chunks then units from a cursor

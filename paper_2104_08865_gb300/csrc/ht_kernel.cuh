@@ -914,7 +914,7 @@ __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KP
       if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
       item = __shfl_sync(kFull, item, 0);
       if (item >= total) break;
-      const unsigned s = find_string_warp(P.item0s, P.count, item, ln);
+      const unsigned s = P.item_str ? __ldg(P.item_str + item) : find_string_warp(P.item0s, P.count, item, ln);
       const StrPlan sp = P.plans[s];
       const uint64_t c = item - sp.item0;
       if (ALIGNED || (((uintptr_t)sp.ptr) & 15u) == 0)
@@ -1126,7 +1126,7 @@ __global__ void __launch_bounds__(1024) plan_totals_kernel(const PlanArgs A) {
     A.ctl->chunks_a = 0;
     A.ctl->units_b = 0;
     A.ctl->unaligned = any_un ? 1u : 0u;
-    if (base_g > A.cap_groups) A.ctl->status = kStatusTooLong;
+    if (base_g > A.cap_groups || (A.item_str && base_i > A.cap_items)) A.ctl->status = kStatusTooLong;
   }
 }
 
@@ -1161,6 +1161,25 @@ __global__ void __launch_bounds__(1024) plan_write_kernel(const PlanArgs A) {
     sp.unitb0 = 0;
     A.plans[i] = sp;
     A.item0s[i] = ei;
+  }
+}
+
+// 4: the string of every work item, so that a batch warp finds its string
+// with one load instead of a search over item0s: one thread per item (grid
+// stride), a binary search over the prefix sums.  (W only gives each width's
+// table its own instance.)
+template <int W>
+__global__ void __launch_bounds__(256) plan_items_kernel(const PlanArgs A) {
+  if (__ldcg(&A.ctl->status) != 0) return;
+  const uint64_t total = __ldcg(&A.ctl->total);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total; it += stride) {
+    unsigned lo = 0, hi = A.count;  // item0s[lo] <= it < item0s[hi]
+    while (hi - lo > 1) {
+      const unsigned mid = (lo + hi) >> 1;
+      if (A.item0s[mid] <= it) lo = mid; else hi = mid;
+    }
+    A.item_str[it] = lo;
   }
 }
 

@@ -18,6 +18,7 @@ inline KernelSet make_kernel_set_v3() {
   ks.batch_unaligned[L - 1] = (const void *)hash_kernel<W, L, false, false, false, B>;
   ks.plan_tiles[L] = (const void *)plan_tiles_kernel<W, L, B>;
   ks.plan_totals = (const void *)plan_totals_kernel<W>;
+  ks.plan_items = (const void *)plan_items_kernel<W>;
   ks.plan_write[L] = (const void *)plan_write_kernel<W, L, B>;
   ks.wait_probe = (const void *)wait_probe_kernel<W>;
   ks.exec_bytes = Dims<W, B>::exec_bytes;

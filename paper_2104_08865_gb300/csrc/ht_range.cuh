@@ -260,6 +260,7 @@ KernelSet make_kernel_set() {
   ks.plan_tiles[2] = (const void *)plan_tiles_kernel<W, 2>;
   ks.plan_tiles[3] = (const void *)plan_tiles_kernel<W, 3>;
   ks.plan_totals = (const void *)plan_totals_kernel<W>;
+  ks.plan_items = (const void *)plan_items_kernel<W>;
   ks.plan_write[0] = (const void *)plan_write_kernel<W, 0>;
   ks.plan_write[1] = (const void *)plan_write_kernel<W, 1>;
   ks.plan_write[2] = (const void *)plan_write_kernel<W, 2>;

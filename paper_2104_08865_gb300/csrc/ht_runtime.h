@@ -34,6 +34,8 @@ struct ht_ctx {
   unsigned long long *tile_items = nullptr;   // multi-block planner, per 1024 strings
   unsigned long long *tile_groups = nullptr;
   unsigned int *tile_flags = nullptr;
+  unsigned int *item_str = nullptr;  // warp-chunk batches: the string of every work item
+  uint64_t cap_items = 0;
   ht::Ctl *ctl = nullptr;
   uint64_t cap_groups = 0, cap_strings = 0;
   // launch shapes: [0..63] by floor(log2(len)), [64] batches
@@ -43,6 +45,7 @@ struct ht_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   cudaGraphNode_t node_plan = nullptr, node_hash = nullptr, node_hash2 = nullptr;
   cudaGraphNode_t node_totals = nullptr, node_write = nullptr;  // multi-block planner (else null)
+  cudaGraphNode_t node_items = nullptr;  // item -> string map (warp-chunk kernel, L >= 2; else null)
   ht_shape graph_shape = {};
   bool graph_valid = false;
   ht::PlanArgs plan_args = {};
