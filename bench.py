@@ -739,7 +739,7 @@ def main():
     ap.add_argument("--no-v3", action="store_true", help="skip the 256-bit-block leg")
     ap.add_argument("--batch-strings", type=int, default=50_000)
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-pool", type=int, default=2 * GIB)
     ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",")],
                     default=[0.1, 0.5, 0.9, 1.2])
