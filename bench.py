@@ -519,8 +519,11 @@ def run_serving(args, dev, stream):
         for _ in range(2):
             abi.ht_server_replay(srv, base + off, ln, [pinned] * nburst, np.zeros(nburst), dig)
             st = abi.ht_server_stats(srv, reset=True)
-            peak = max(peak, st["bytes_completed"] / st["wall_s"] / 1e9)
+            gbs = st["bytes_completed"] / st["wall_s"] / 1e9
+            if gbs > peak:
+                peak, peak_batches = gbs, st["batches"]
         res["peak_gbs"] = round(peak, 1)
+        res["peak_batches"] = int(peak_batches)
         mean_len = float(inputs.log_uniform_lengths(62, 100000, 256, 64 << 20).mean())
         res["points"] = []
         for frac in args.serve_loads:
@@ -535,7 +538,7 @@ def run_serving(args, dev, stream):
             res["points"].append({"load": frac, "offered_gbs": round(frac * peak, 1),
                                   "requests": n, "achieved_gbs": round(st["bytes_completed"] / st["wall_s"] / 1e9, 1),
                                   "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
-                                  "max_submit_delay_us": round(late, 1)})
+                                  "max_submit_delay_us": round(late, 1), "batches": int(st["batches"])})
         abi.ht_server_destroy(srv)
         out["forms"][form] = res
     out["mean_len_bytes"] = round(mean_len)

@@ -583,8 +583,24 @@ struct BatchNodes {
 
 // The general (unaligned-capable) batch kernel paired with the aligned-only
 // one of a shape (none for the stream kernel, which handles both).
-static const void *general_batch_kernel(const ht_ctx *c, const ht_shape &shape) {
-  return shape.kernel == 2 ? c->ks->range_batch_unaligned : c->ks->batch_unaligned[shape.chunk_levels - 1];
+static const void *general_batch_kernel(const ht_ctx *c, const ht_shape &shape, bool map) {
+  if (shape.kernel == 2) return c->ks->range_batch_unaligned;
+  return map ? c->ks->batch_unaligned_map[shape.chunk_levels - 1] : c->ks->batch_unaligned[shape.chunk_levels - 1];
+}
+
+// Batches of at least this many strings find each work item's string in an
+// item map that a fourth planner kernel writes (one load per item instead of
+// a 32-way search over the prefix sums, 3 to 4 dependent loads at these
+// sizes).  Measured on GB300: 2-3 % faster for 50,000 strings of up to
+// 1 MiB and for 200,000 short strings; batches of a few thousand large
+// strings (serving) are faster with the search (the search kernel keeps
+// its code, the map costs a launch).
+constexpr size_t kMapMinStrings = 16384;
+
+// Whether a batch of `count` strings under `shape` uses the item map.
+static bool use_map(const ht_ctx *c, const ht_shape &shape, size_t count) {
+  return shape.kernel == 1 && shape.chunk_levels >= 2 && count >= kMapMinStrings &&
+         c->ks->batch_map[shape.chunk_levels - 1] != nullptr;
 }
 
 static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
@@ -592,7 +608,7 @@ static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
   const int pl = shape.kernel == 1 ? shape.chunk_levels : 0;
   n.multi = shape.kernel != 2;
   n.general = shape.kernel != 0;
-  n.map = shape.kernel == 1 && shape.chunk_levels >= 2;
+  n.map = use_map(c, shape, c->plan_args.count);
   c->plan_args.item_str = n.map ? c->item_str : nullptr;
   c->plan_args.cap_items = n.map ? c->cap_items : 0;
   c->batch_params.item_str = n.map ? c->item_str : nullptr;
@@ -627,7 +643,7 @@ static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
   } else if (shape.kernel == 2) {
     func = ks.range_batch;
   } else {
-    func = ks.batch[shape.chunk_levels - 1];
+    func = n.map ? ks.batch_map[shape.chunk_levels - 1] : ks.batch[shape.chunk_levels - 1];
   }
   const int tpb = shape.threads_per_block;
   const int bps = std::max(1, std::min(shape.blocks_per_sm, occupancy(func, tpb, smem)));
@@ -641,7 +657,7 @@ static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
   n.hargs[0] = &c->batch_params;
   n.hash.kernelParams = n.hargs;
   n.hash2 = n.hash;
-  if (n.general) n.hash2.func = (void *)general_batch_kernel(c, shape);
+  if (n.general) n.hash2.func = (void *)general_batch_kernel(c, shape, n.map);
 }
 
 static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
@@ -673,6 +689,7 @@ static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
   }
   HT_CUDA(cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
   c->graph_shape = shape;
+  c->graph_map = n.map;
   c->graph_valid = true;
   return HT_OK;
 }
@@ -708,7 +725,8 @@ int ht_hash_batch(ht_ctx *c, const void *const *ptrs, const uint64_t *lens, size
   P.unitb0s = c->unitb0s;
   P.digests = (unsigned long long *)digests;
   P.count = (unsigned)count;
-  if (!c->graph_valid || memcmp(&c->graph_shape, &shape, sizeof shape) != 0) {
+  if (!c->graph_valid || memcmp(&c->graph_shape, &shape, sizeof shape) != 0 ||
+      c->graph_map != use_map(c, shape, count)) {
     int rc = build_batch_graph(c, shape);
     if (rc) return rc;
   } else {

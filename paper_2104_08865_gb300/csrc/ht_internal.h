@@ -112,6 +112,8 @@ struct KernelSet {
   const void *single_unaligned[3];  // [L-1]
   const void *batch[3];             // [L-1], aligned-only
   const void *batch_unaligned[3];   // [L-1], general (see ctl.unaligned)
+  const void *batch_map[3];         // [L-1], L >= 2: the same, strings found through the item map
+  const void *batch_unaligned_map[3];
   const void *plan[4];              // [0]: stream, [L]: warp-chunk (one block, hybrid work list too)
   const void *plan_tiles[4];        // multi-block planner, same index: tile totals
   const void *plan_totals;          //   their prefix sums and the batch totals

@@ -887,7 +887,10 @@ __device__ __forceinline__ bool exit_protocol(const KParams &P, int ln) {
 }
 
 // B: words per block, 8 (the default, 512-bit blocks) or 4 (256-bit blocks).
-template <int W, int L, bool SINGLE, bool ALIGNED, bool INC = false, int B = kLanes>
+// MAP (batches): find each work item's string in the planner's item map
+// (one load) instead of searching the prefix sums; a separate instance,
+// used for batches of many strings, so that the searching one keeps its code.
+template <int W, int L, bool SINGLE, bool ALIGNED, bool INC = false, int B = kLanes, bool MAP = false>
 __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KParams P) {
   static_assert(!INC || (SINGLE && L == 2), "incremental updates hash one string in 64-execution chunks");
   const int ln = threadIdx.x & 31;
@@ -914,7 +917,9 @@ __global__ void __launch_bounds__(256, 2) hash_kernel(const __grid_constant__ KP
       if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
       item = __shfl_sync(kFull, item, 0);
       if (item >= total) break;
-      const unsigned s = P.item_str ? __ldg(P.item_str + item) : find_string_warp(P.item0s, P.count, item, ln);
+      unsigned s;
+      if constexpr (MAP) s = __ldg(P.item_str + item);
+      else s = find_string_warp(P.item0s, P.count, item, ln);
       const StrPlan sp = P.plans[s];
       const uint64_t c = item - sp.item0;
       if (ALIGNED || (((uintptr_t)sp.ptr) & 15u) == 0)

@@ -16,6 +16,8 @@ inline KernelSet make_kernel_set_v3() {
   ks.single_unaligned[L - 1] = (const void *)hash_kernel<W, L, true, false, false, B>;
   ks.batch[L - 1] = (const void *)hash_kernel<W, L, false, true, false, B>;
   ks.batch_unaligned[L - 1] = (const void *)hash_kernel<W, L, false, false, false, B>;
+  ks.batch_map[L - 1] = (const void *)hash_kernel<W, L, false, true, false, B, true>;
+  ks.batch_unaligned_map[L - 1] = (const void *)hash_kernel<W, L, false, false, false, B, true>;
   ks.plan_tiles[L] = (const void *)plan_tiles_kernel<W, L, B>;
   ks.plan_totals = (const void *)plan_totals_kernel<W>;
   ks.plan_items = (const void *)plan_items_kernel<W>;

@@ -251,6 +251,12 @@ KernelSet make_kernel_set() {
   ks.batch_unaligned[0] = (const void *)hash_kernel<W, 1, false, false>;
   ks.batch_unaligned[1] = (const void *)hash_kernel<W, 2, false, false>;
   ks.batch_unaligned[2] = (const void *)hash_kernel<W, 3, false, false>;
+  ks.batch_map[0] = nullptr;
+  ks.batch_map[1] = (const void *)hash_kernel<W, 2, false, true, false, kLanes, true>;
+  ks.batch_map[2] = (const void *)hash_kernel<W, 3, false, true, false, kLanes, true>;
+  ks.batch_unaligned_map[0] = nullptr;
+  ks.batch_unaligned_map[1] = (const void *)hash_kernel<W, 2, false, false, false, kLanes, true>;
+  ks.batch_unaligned_map[2] = (const void *)hash_kernel<W, 3, false, false, false, kLanes, true>;
   ks.plan[0] = (const void *)plan_kernel<W, 0>;
   ks.plan[1] = (const void *)plan_kernel<W, 1>;
   ks.plan[2] = (const void *)plan_kernel<W, 2>;

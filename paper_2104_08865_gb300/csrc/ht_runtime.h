@@ -47,6 +47,7 @@ struct ht_ctx {
   cudaGraphNode_t node_totals = nullptr, node_write = nullptr;  // multi-block planner (else null)
   cudaGraphNode_t node_items = nullptr;  // item -> string map (warp-chunk kernel, L >= 2; else null)
   ht_shape graph_shape = {};
+  bool graph_map = false;  // the graph's planner writes the item map and its kernels read it
   bool graph_valid = false;
   ht::PlanArgs plan_args = {};
   ht::KParams batch_params = {};

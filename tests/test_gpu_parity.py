@@ -228,10 +228,19 @@ def test_launch_counter_counts_kernels(dev):
     from paper_2104_08865_gb300 import abi
     batch_kernel = abi.ht_get_shape(h.ctx, 2**64 - 1)["kernel"]
     # one hash kernel, then the planner (three launches, one for the hybrid
-    # family, four with the item -> string map of the warp-chunk family) and
-    # the batch kernels (an aligned and a general one, except for the stream
-    # family)
-    assert h.launches() - before == 1 + {0: 4, 1: 6, 2: 3}[batch_kernel]
+    # family) and the batch kernels (an aligned and a general one, except for
+    # the stream family)
+    assert h.launches() - before == 1 + {0: 4, 1: 5, 2: 3}[batch_kernel]
+    if batch_kernel == 1:
+        # a batch of 16,384 strings or more: a fourth planner launch writes
+        # the item -> string map
+        n = 20_000
+        ptrs = torch.full((n,), dbuf.data_ptr(), dtype=torch.int64, device=dev)
+        ln = torch.full((n,), 100, dtype=torch.int64, device=dev)
+        before = h.launches()
+        h.hash_batch(ptrs, ln, n)
+        torch.cuda.synchronize()
+        assert h.launches() - before == 6
 
 
 def test_python_layer_rejects_bad_tensors(dev):
