@@ -1,7 +1,8 @@
 """Cases run against the checked build (libhalftime_check.so, loaded with
 HALFTIME_CHECKED=1 in a process of its own by test_gpu_checked.py): the
 range checks must never fire, and every digest must still equal the
-oracle's.  Prints "checked: ok" at the end."""
+oracle's -- single strings, batches (with and without the planner's item
+map), incremental pieces and split parts.  Prints "checked: ok" at the end."""
 import os
 import sys
 
@@ -70,6 +71,25 @@ for b in (8, 4):
                                for o, n in zip(offs, lens)])
                 assert np.array_equal(got, w2), ("unaligned batch", b, width)
         h.close()
+
+# 2b. a batch of 20,000 strings: the planner's item map and the batch kernel
+#     instance that reads it
+for b in (8, 4):
+    h, ref = pair(24, b)
+    rng = np.random.default_rng(b)
+    lens = [int(v) for v in rng.integers(0, 3000, 20_000)]
+    lens[::1000] = [200_000] * 20  # a few strings of several work items
+    buf, offs = inputs.packed_batch(33, lens)
+    want = oracle.hash_many(24, ref, buf, offs, lens, b=b)
+    dbuf = torch.from_numpy(buf).to(dev)
+    ptrs = torch.tensor([dbuf.data_ptr() + int(o) for o in offs], dtype=torch.int64, device=dev)
+    ln = torch.tensor(lens, dtype=torch.int64, device=dev)
+    before = h.launches()
+    got = u64(h.hash_batch(ptrs, ln, len(lens)))
+    h.status()
+    assert h.launches() - before == 6  # four planner launches, two batch kernels
+    assert np.array_equal(got, want), ("item-map batch", b)
+    h.close()
 
 # 3. incremental pieces and a string in two parts (512-bit blocks)
 for width in (16, 40):
