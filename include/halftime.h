@@ -490,8 +490,11 @@ typedef struct ht_server_opts {
   uint64_t max_wait_us;   /* longest a request waits for batch-mates (default 0) */
   int pinned_mode;        /* pinned-host requests: 0 (default) = read in place by the
                              batch kernel when the GPU can address the memory (on
-                             GB300 the coherent CPU-GPU link), else staged; 1 = always
-                             staged, copied into a device arena first */
+                             GB300 the coherent CPU-GPU link), else staged; the
+                             batch descriptors and digests then stay in pinned host
+                             memory too (no copies around a batch); 1 = always
+                             staged, copied into a device arena first, with the
+                             descriptors and digests copied as well */
 } ht_server_opts;
 
 typedef struct ht_server_stats_t {

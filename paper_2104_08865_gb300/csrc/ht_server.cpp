@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -106,6 +107,13 @@ struct Slot {
   const void **d_ptrs = nullptr;
   uint64_t *d_lens = nullptr;
   uint64_t *d_digests = nullptr;
+  // device views of h_ptrs, h_lens and h_digests when the GPU can address
+  // pinned host memory (and requests are not forced through staging): the
+  // planner then reads the descriptors and the batch kernel writes the
+  // digests in place, with no copy in either direction (else null)
+  const void **m_ptrs = nullptr;
+  uint64_t *m_lens = nullptr;
+  uint64_t *m_digests = nullptr;
   std::vector<uint64_t> tickets;
   uint64_t bytes = 0;
   int64_t fake_deadline = 0;
@@ -159,14 +167,23 @@ int launch_real(ht_server *S, Slot &sl, const std::vector<Req *> &batch) {
     }
     sl.h_lens[i] = r->len;
   }
-  cudaError_t e = cudaMemcpyAsync(sl.d_ptrs, sl.h_ptrs, n * sizeof(void *), cudaMemcpyHostToDevice, sl.stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.d_lens, sl.h_lens, n * sizeof(uint64_t), cudaMemcpyHostToDevice, sl.stream);
-  if (e != cudaSuccess) return ht::cuda_error(e, "batch descriptor copy");
-  int rc = ht_hash_batch(sl.ctx, sl.d_ptrs, sl.d_lens, n, sl.d_digests, sl.stream);
-  if (rc) return rc;
-  e = cudaMemcpyAsync(sl.h_digests, sl.d_digests, n * S->k * sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                      sl.stream);
+  cudaError_t e = cudaSuccess;
+  if (sl.m_ptrs) {
+    // descriptors read and digests written in place: the batch graph is the
+    // only work of the batch (the stores above precede the launch)
+    std::atomic_thread_fence(std::memory_order_release);
+    int rc = ht_hash_batch(sl.ctx, sl.m_ptrs, sl.m_lens, n, sl.m_digests, sl.stream);
+    if (rc) return rc;
+  } else {
+    e = cudaMemcpyAsync(sl.d_ptrs, sl.h_ptrs, n * sizeof(void *), cudaMemcpyHostToDevice, sl.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(sl.d_lens, sl.h_lens, n * sizeof(uint64_t), cudaMemcpyHostToDevice, sl.stream);
+    if (e != cudaSuccess) return ht::cuda_error(e, "batch descriptor copy");
+    int rc = ht_hash_batch(sl.ctx, sl.d_ptrs, sl.d_lens, n, sl.d_digests, sl.stream);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(sl.h_digests, sl.d_digests, n * S->k * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                        sl.stream);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
   if (e != cudaSuccess) return ht::cuda_error(e, "batch digest copy");
   return HT_OK;
@@ -387,6 +404,19 @@ int make_server(ht_server *S, ht_ctx *ctx, uint64_t budget, const ht_server_opts
     if (e == cudaSuccess) e = cudaMalloc((void **)&sl.d_lens, o.max_batch * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&sl.d_digests, o.max_batch * S->k * sizeof(uint64_t));
     if (e != cudaSuccess) return ht::cuda_error(e, "server slot");
+    if (o.pinned_mode == 0) {
+      // the same buffers as the GPU sees them, if it can address them
+      void *mp = nullptr, *ml = nullptr, *md = nullptr;
+      if (cudaHostGetDevicePointer(&mp, (void *)sl.h_ptrs, 0) == cudaSuccess &&
+          cudaHostGetDevicePointer(&ml, sl.h_lens, 0) == cudaSuccess &&
+          cudaHostGetDevicePointer(&md, sl.h_digests, 0) == cudaSuccess) {
+        sl.m_ptrs = static_cast<const void **>(mp);
+        sl.m_lens = static_cast<uint64_t *>(ml);
+        sl.m_digests = static_cast<uint64_t *>(md);
+      } else {
+        cudaGetLastError();  // (not mapped: the descriptors are copied)
+      }
+    }
   }
   return HT_OK;
 }
