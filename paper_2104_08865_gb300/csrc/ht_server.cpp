@@ -150,7 +150,10 @@ struct ht_server {
 
 namespace {
 
-// Enqueues copies, the batch hash and the digest copy of a formed batch.
+// Enqueues a formed batch: staging copies of pinned requests that the GPU
+// cannot read in place, then one single-string launch (a lone request) or the
+// batch graph, with descriptor and digest copies only where the GPU cannot
+// address the slot's pinned buffers, then the slot's completion event.
 int launch_real(ht_server *S, Slot &sl, const std::vector<Req *> &batch) {
   const size_t n = batch.size();
   for (size_t i = 0; i < n; ++i) {
@@ -168,7 +171,15 @@ int launch_real(ht_server *S, Slot &sl, const std::vector<Req *> &batch) {
     sl.h_lens[i] = r->len;
   }
   cudaError_t e = cudaSuccess;
-  if (sl.m_ptrs) {
+  if (n == 1) {
+    // a lone request (common at low load): one single-string launch instead
+    // of the batch graph's planner and batch kernels (about 25 us less)
+    uint64_t *dig = sl.m_digests ? sl.m_digests : sl.d_digests;
+    int rc = ht_hash(sl.ctx, sl.h_ptrs[0], sl.h_lens[0], dig, sl.stream);
+    if (rc) return rc;
+    if (!sl.m_digests)
+      e = cudaMemcpyAsync(sl.h_digests, sl.d_digests, S->k * sizeof(uint64_t), cudaMemcpyDeviceToHost, sl.stream);
+  } else if (sl.m_ptrs) {
     // descriptors read and digests written in place: the batch graph is the
     // only work of the batch (the stores above precede the launch)
     std::atomic_thread_fence(std::memory_order_release);
