@@ -477,8 +477,11 @@ uint64_t ht_ctx_launches(ht_ctx *ctx);
  * A server admits hash requests as they arrive and keeps the GPU busy with
  * overlapping batches: a dispatcher thread forms a batch of the requests
  * that fit the free device memory (the budget) and a free stream slot,
- * stages pinned-host requests into a device arena, launches the batch graph
- * on that slot's stream and copies the digests back; a completion thread
+ * stages pinned-host requests the GPU cannot read in place into a device
+ * arena, and launches the batch on that slot's stream -- the batch graph,
+ * or one single-string launch for a batch of one request -- with the
+ * batch's descriptors and digests in pinned host memory the GPU reads and
+ * writes in place (else copied there and back); a completion thread
  * retires batches as their events fire, releases their memory and wakes
  * waiters.  Seeds and in-flight tree state stay on the device.  Every
  * request's arrival, launch and completion times are recorded (host
