@@ -64,6 +64,10 @@ def lib() -> ctypes.CDLL:
                                         ctypes.c_void_p, ctypes.c_uint64, u64p,
                                         ctypes.POINTER(ctypes.c_int)]
             L.htref_params.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 5
+            L.htref_seed_words_badger.restype = ctypes.c_size_t
+            L.htref_seed_words_badger.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.htref_hash_badger.argtypes = [ctypes.c_int, ctypes.c_int, u64p, ctypes.c_size_t,
+                                            ctypes.c_void_p, ctypes.c_uint64, u64p]
             _lib = L
     return _lib
 
@@ -165,4 +169,37 @@ def hash_many(width: int, seeds: np.ndarray, buf: np.ndarray, offsets, lengths, 
                              row.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), None)
         if rc:
             raise ValueError("htref_hash failed: %d" % rc)
+    return out
+
+
+# ---- ablation: Badger's binary tree without a final NH (Section 5.2) ----------
+
+def seed_words_badger(width: int, b: int = 8) -> int:
+    """Seed words of the binary-tree ablation: E, 64 level keys per tree, R."""
+    return int(lib().htref_seed_words_badger(width, b))
+
+
+def hash_bytes_badger(width: int, seeds: np.ndarray, data, *, b: int = 8) -> np.ndarray:
+    """Digest of one string under the binary-tree ablation (Eq. algebraic-badger
+    over all EHC outputs of a tree, lane-minor; Toeplitz tail as usual)."""
+    p = params(width)
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    ptr, n, keep = _bytes_ptr(data)
+    dig = np.zeros(p["k"], dtype=np.uint64)
+    rc = lib().htref_hash_badger(width, b, _u64p(seeds), seeds.size, ptr if n else None, n, _u64p(dig))
+    if rc:
+        raise ValueError("htref_hash_badger failed: %d" % rc)
+    return dig
+
+
+def hash_many_badger(width: int, seeds: np.ndarray, buf: np.ndarray, offsets, lengths,
+                     b: int = 8) -> np.ndarray:
+    """Digests of slices of buf under the binary-tree ablation -> uint64[count, k]."""
+    p = params(width)
+    buf = np.ascontiguousarray(buf).view(np.uint8).reshape(-1)
+    out = np.zeros((len(lengths), p["k"]), dtype=np.uint64)
+    for i, (o, n) in enumerate(zip(offsets, lengths)):
+        o = int(o); n = int(n)
+        assert o + n <= buf.size
+        out[i] = hash_bytes_badger(width, seeds, buf[o:o + n], b=b)
     return out

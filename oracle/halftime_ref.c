@@ -410,3 +410,85 @@ int htref_hash(int width, const uint64_t *seeds, size_t n_words,
                const uint8_t *data, uint64_t len, uint64_t *digest) {
   return htref_hash_bf(width, 8, 8, 0, seeds, n_words, data, len, digest, NULL);
 }
+
+/* ---- ablation: Badger's binary tree without a final NH (Section 5.2) ----- */
+
+#define REF_BADGER_LEVELS 64 /* T keys per tree: a node spans < 2^64 leaves */
+
+size_t htref_seed_words_badger(int width, int b) {
+  width_spec s;
+  if (get_spec(width, &s) || b < 1 || b > 8) return 0;
+  return (size_t)s.e * REF_W + (size_t)s.k * REF_BADGER_LEVELS +
+         (size_t)b * s.d * REF_W + s.k;
+}
+
+/* ceil(lg n) for n >= 1 */
+static int ceil_lg(uint64_t n) {
+  int m = 0;
+  while (m < 64 && ((uint64_t)1 << m) < n) m++;
+  return m;
+}
+
+/* Eq. algebraic-badger over the leaves s[0, n), n >= 1: a single leaf is
+ * itself; a longer span splits after its first 2^(ceil(lg n) - 1) leaves and
+ * H(k_i, left, right) = NH(left, k_i) + right joins the two halves, with
+ * i = ceil(lg n) - 1. */
+static uint64_t badger_T(const uint64_t *keys, const uint64_t *s, uint64_t n) {
+  if (n == 1) return s[0];
+  const int i = ceil_lg(n) - 1;
+  const uint64_t half = (uint64_t)1 << i;
+  return htref_nh_word(badger_T(keys, s, half), keys[i]) +
+         badger_T(keys, s + half, n - half);
+}
+
+int htref_hash_badger(int width, int b, const uint64_t *seeds, size_t n_words,
+                      const uint8_t *data, uint64_t len, uint64_t *digest) {
+  width_spec s;
+  if (get_spec(width, &s)) return HTREF_ERR_WIDTH;
+  if (b < 1 || b > 8) return HTREF_ERR_ARG;
+  if (n_words != htref_seed_words_badger(width, b) || seeds == NULL || digest == NULL)
+    return HTREF_ERR_ARG;
+  if (len > 0 && data == NULL) return HTREF_ERR_ARG;
+  const int k = s.k;
+  const size_t off_T = (size_t)s.e * REF_W;
+  const size_t off_R = off_T + (size_t)k * REF_BADGER_LEVELS;
+  const size_t exec_bytes = 8 * (size_t)b * s.d * REF_W;
+  const uint64_t N = len / exec_bytes;
+  const uint64_t n_leaves = N * (uint64_t)b;
+
+  /* EHC of every execution and lane: leaf x*b + lane of tree t */
+  uint64_t *leaves = NULL;
+  if (n_leaves) {
+    leaves = malloc((size_t)k * n_leaves * sizeof(uint64_t));
+    if (!leaves) return HTREF_ERR_ARG;
+    for (uint64_t x = 0; x < N; x++)
+      for (int lane = 0; lane < b; lane++) {
+        uint64_t y[5];
+        ehc_lane(&s, b, seeds, data + x * exec_bytes, lane, y);
+        for (int t = 0; t < k; t++) leaves[(size_t)t * n_leaves + x * b + lane] = y[t];
+      }
+  }
+  for (int t = 0; t < k; t++)
+    digest[t] = n_leaves ? badger_T(seeds + off_T + (size_t)t * REF_BADGER_LEVELS,
+                                    leaves + (size_t)t * n_leaves, n_leaves)
+                         : 0;
+  free(leaves);
+
+  /* Tail NH with Toeplitz keys (Section 6.1), length word appended */
+  const uint64_t tail_start = N * exec_bytes;
+  const uint64_t tail_len = len - tail_start;
+  const uint64_t M = (tail_len + 7) / 8;
+  for (uint64_t m = 0; m <= M; m++) {
+    uint64_t word;
+    if (m == M) {
+      word = len;
+    } else {
+      uint8_t buf[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      uint64_t avail = tail_len - 8 * m;
+      memcpy(buf, data + tail_start + 8 * m, avail < 8 ? (size_t)avail : 8);
+      word = load_le64(buf);
+    }
+    for (int t = 0; t < k; t++) digest[t] += htref_nh_word(word, seeds[off_R + t + m]);
+  }
+  return HTREF_OK;
+}

@@ -78,6 +78,21 @@ int htref_hash_bf(int width_bytes, int b, int f, int recursive,
                   const uint8_t *data, uint64_t len, uint64_t *digest,
                   int *level_counts);
 
+/* The ablation of Section 5.2: Badger's binary tree T (Eq. algebraic-badger)
+ * consumes the EHC outputs whole, with no pending roots and no final NH.
+ * Per tree t the leaves are the EHC outputs y_t of every execution and lane,
+ * execution-major and lane-minor (leaf x*b + lane); T splits a span of n > 1
+ * leaves at 2^(ceil(lg n) - 1) and joins the halves with the fan-out-2 node
+ * H(k_i, x, y) = NH(x, k_i) + y, i = ceil(lg n) - 1 (Section 3.1, Section 3.2
+ * node variant).  Output t = T_t (0 without leaves) + the Toeplitz tail NH with
+ * the length word, as in the default hash.
+ * Seed layout: E: e*w words, T: k*64 level keys (key i of tree t at
+ * e*w + 64*t + i), R: b*d*w + k. */
+size_t htref_seed_words_badger(int width_bytes, int b);
+int htref_hash_badger(int width_bytes, int b, const uint64_t *seed_words,
+                      size_t n_words, const uint8_t *data, uint64_t len,
+                      uint64_t *digest);
+
 /* Parameters of a width: fills {d, e, k, w, exec_bytes(b=8)}. */
 int htref_params(int width_bytes, int *d, int *e, int *k, int *w,
                  int *exec_bytes);
