@@ -42,7 +42,7 @@ typedef struct ht_table ht_table;
 /* ---- status codes -------------------------------------------------------- */
 #define HT_OK 0
 #define HT_ERR_ARG -1      /* invalid argument (NULL pointer, size mismatch) */
-#define HT_ERR_WIDTH -2    /* width not in {16, 24, 32, 40} (optionally | HT_BLOCK_256) */
+#define HT_ERR_WIDTH -2    /* width not in {16, 24, 32, 40} (optionally | HT_BLOCK_256 or | HT_TREE_BINARY) */
 #define HT_ERR_TOO_LONG -3 /* input or batch exceeds the context's capacity */
 #define HT_ERR_CUDA -4     /* a CUDA runtime call failed (message has detail) */
 #define HT_ERR_NOMEM -5    /* device or host allocation failed */
@@ -81,6 +81,25 @@ size_t ht_seed_words(int width_bytes);
  * chunk_levels 2; ht_autotune tunes its launch size); ht_inc_create,
  * ht_part_begin and ht_hash_noalloc reject it with HT_ERR_WIDTH. */
 #define HT_BLOCK_256 0x100
+
+/* ---- tree: the paper's T-hat (default) or the binary-tree ablation -------
+ * A width_bytes argument may instead carry HT_TREE_BINARY (width_bytes |
+ * HT_TREE_BINARY; not together with HT_BLOCK_256) to select the ablation
+ * that the paper measures its tree against (Section 5.2, closing
+ * paragraph: Badger's approach): per output word, Carter and Wegman's binary
+ * tree T (Eq. algebraic-badger, Section 3.1) consumes the EHC outputs of all
+ * executions and lanes whole (execution-major, lane-minor), with the
+ * fan-out-2 NH node of Section 3.2 and one key per level; there is no final
+ * NH over pending roots.  The Toeplitz tail with the length word is added as
+ * in the default hash.  Seed layout: E (e*w words), 64 level keys per output
+ * word, R (8*d*w + k): 295 / 390 / 458 / 472 words for widths 16 / 24 / 32 /
+ * 40.  Digests differ from the default's.  A context created with
+ * HT_TREE_BINARY serves ht_hash, ht_hash_host, ht_hash_batch,
+ * ht_hash_batch_naive, the server and the digest table, with the warp-chunk
+ * kernel and 64-execution items only (ht_set_shape accepts kernel 1 with
+ * chunk_levels 2; ht_autotune tunes its launch size); ht_inc_create,
+ * ht_part_begin and ht_hash_noalloc reject it with HT_ERR_WIDTH. */
+#define HT_TREE_BINARY 0x200
 
 /* Expands a 64-bit seed into the seed words of a width on the host: word i
  * is the i-th output of splitmix64 (Steele, Lea, Flood, OOPSLA 2014) started
@@ -463,6 +482,20 @@ typedef struct ht_shape {
  * writes it to *best if best is not NULL.  Synchronous.  Errors: HT_ERR_ARG,
  * HT_ERR_NOMEM, HT_ERR_CUDA. */
 int ht_autotune(ht_ctx *ctx, uint64_t len, ht_stream_t stream, ht_shape *best);
+
+/* The same for batches (the persistent kernel of ht_hash_batch): times every
+ * candidate batch shape -- kernel family, chunk height L (executions per
+ * work item, 8^L: the parallelism a string gets), threads per block and
+ * blocks per SM -- on the caller's own batch, and stores the fastest as the
+ * context's batch shape (the one ht_hash_batch and servers created from this
+ * context use).  Arguments as for ht_hash_batch; digests_dev receives the
+ * batch's digests (from the last run: the same for every shape).  A shape
+ * whose planner finds that the batch does not fit the reserved scratch is
+ * skipped.  Synchronous (several replays of the batch per candidate).
+ * Errors: HT_ERR_ARG, HT_ERR_TOO_LONG (no shape fits), HT_ERR_CUDA. */
+int ht_autotune_batch(ht_ctx *ctx, const void *const *ptrs_dev, const uint64_t *lens_dev,
+                      size_t count, uint64_t *digests_dev, ht_stream_t stream,
+                      ht_shape *best);
 
 /* Reads / overrides the cached shape of the bucket of `len`
  * (len = UINT64_MAX selects the batch shape).  Errors: HT_ERR_ARG. */

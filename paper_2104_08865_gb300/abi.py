@@ -38,6 +38,8 @@ HT_ERR_DEVICE = -9
 WIDTHS = (16, 24, 32, 40)
 # width_bytes | HT_BLOCK_256 selects blocks of 4 words (256 bits) instead of 8
 HT_BLOCK_256 = 0x100
+# width_bytes | HT_TREE_BINARY selects the binary-tree ablation (Badger's tree, no final NH)
+HT_TREE_BINARY = 0x200
 HT_BUILD_CHECKED = 1
 
 
@@ -120,6 +122,7 @@ _PROTOS = {
     "ht_part_merge": (_int, [_vp, _vp, _sz, _vp]),
     "ht_finish_parts": (_int, [_vp, _vp, _vp]),
     "ht_autotune": (_int, [_vp, _u64, _vp, ctypes.POINTER(ht_shape)]),
+    "ht_autotune_batch": (_int, [_vp, _vp, _vp, _sz, _vp, _vp, ctypes.POINTER(ht_shape)]),
     "ht_get_shape": (_int, [_vp, _u64, ctypes.POINTER(ht_shape)]),
     "ht_set_shape": (_int, [_vp, _u64, ctypes.POINTER(ht_shape)]),
     "ht_ctx_launches": (_u64, [_vp]),
@@ -413,6 +416,14 @@ def ht_finish_parts(ctx: int, digest_dev, stream=None) -> None:
 def ht_autotune(ctx: int, length: int, stream=None) -> dict:
     best = ht_shape()
     _check(_lib.ht_autotune(ctx, length, _stream(stream), ctypes.byref(best)))
+    return {n: getattr(best, n) for n, _ in ht_shape._fields_}
+
+
+def ht_autotune_batch(ctx: int, ptrs_dev, lens_dev, count: int, digests_dev, stream=None) -> dict:
+    """Times the candidate batch shapes on this batch; keeps the fastest."""
+    best = ht_shape()
+    _check(_lib.ht_autotune_batch(ctx, _ptr(ptrs_dev), _ptr(lens_dev), count, _ptr(digests_dev),
+                                  _stream(stream), ctypes.byref(best)))
     return {n: getattr(best, n) for n, _ in ht_shape._fields_}
 
 

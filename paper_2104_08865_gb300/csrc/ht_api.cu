@@ -68,6 +68,10 @@ const KernelSet *kernel_set(int width) {
     case 24 | HT_BLOCK_256: return &kernels_w24_v3();
     case 32 | HT_BLOCK_256: return &kernels_w32_v3();
     case 40 | HT_BLOCK_256: return &kernels_w40_v3();
+    case 16 | HT_TREE_BINARY: return &kernels_w16_bin();
+    case 24 | HT_TREE_BINARY: return &kernels_w24_bin();
+    case 32 | HT_TREE_BINARY: return &kernels_w32_bin();
+    case 40 | HT_TREE_BINARY: return &kernels_w40_bin();
     default: return nullptr;
   }
 }
@@ -233,8 +237,14 @@ void fill_keys(const ht_ctx *c, KParams &P) {
   const KernelSet &ks = *c->ks;
   memset(&P, 0, sizeof P);
   for (int i = 0; i < ks.ew; ++i) P.E[i] = c->h_seeds[i];
-  for (int t = 0; t < ks.k; ++t)
-    for (int i = 0; i < 7; ++i) P.T0[t][i] = c->h_seeds[ks.off_T + t * 19 * 7 + i];
+  if (ks.tree) {
+    // binary-tree ablation: level keys k_0 .. k_7 of every tree
+    for (int t = 0; t < ks.k; ++t)
+      for (int i = 0; i < 8; ++i) P.T0[t][i] = c->h_seeds[ks.off_T + t * kBinLevels + i];
+  } else {
+    for (int t = 0; t < ks.k; ++t)
+      for (int i = 0; i < 7; ++i) P.T0[t][i] = c->h_seeds[ks.off_T + t * 19 * 7 + i];
+  }
   P.seeds = c->d_seeds;
   P.scr = scratch_view(c);
 }
@@ -254,6 +264,15 @@ static int occupancy(const void *func, int tpb, size_t smem) {
   return n;
 }
 
+// The same, remembered by the context.
+static int occupancy(ht_ctx *c, const void *func, int tpb, size_t smem) {
+  for (const auto &o : c->occ_cache)
+    if (o.func == func && o.tpb == tpb && o.smem == smem) return o.blocks;
+  const int n = occupancy(func, tpb, smem);
+  c->occ_cache.push_back({func, tpb, smem, n});
+  return n;
+}
+
 // The warp-chunk kernel with 64-execution chunks measured fastest on GB300
 // for long strings (the autotuner confirms or overrides per length bucket).
 static ht_shape default_shape() {
@@ -266,12 +285,25 @@ static ht_shape default_shape() {
   return s;
 }
 
+// Strings below 32 MiB (length buckets up to 24) take 8-execution chunks
+// where the kernel set has them: one execution per thread instead of eight
+// in a row, eight times the warps.  Measured on GB300 (widths 24 and 40,
+// back-to-back launches): 64 KiB 8.2-12.3 us instead of 12.3-14.4, 1 MiB
+// 12.3-13.4 instead of 18.5-20.5, 16 MiB 16.4-17.0 instead of 22.0-22.6; at
+// 64 MiB 64-execution chunks are faster again.
+static ht_shape default_shape(const KernelSet &ks, int bucket) {
+  ht_shape s = default_shape();
+  if (bucket <= 24 && ks.single_aligned[0]) s.chunk_levels = 1;
+  return s;
+}
+
 static bool shape_ok(const KernelSet &ks, const ht_shape &s) {
   if (s.threads_per_block < 32 || s.threads_per_block % 32 != 0 || s.blocks_per_sm < 1 ||
       s.blocks_per_sm > 32)
     return false;
-  // 256-bit blocks: the warp-chunk kernel with 64-execution sub-chunks only
-  if (ks.lanes != kLanes) return s.kernel == 1 && s.chunk_levels == 2 && s.threads_per_block <= 256;
+  // 256-bit blocks and the binary-tree ablation: the warp-chunk kernel with
+  // 64-execution items only
+  if (ks.lanes != kLanes || ks.tree) return s.kernel == 1 && s.chunk_levels == 2 && s.threads_per_block <= 256;
   if (s.kernel == 0) return s.stages >= 2 && s.stages <= 8 && s.threads_per_block <= 256;
   if (s.kernel == 1)
     return s.chunk_levels >= 1 && s.chunk_levels <= 3 && s.threads_per_block <= 256;
@@ -288,7 +320,8 @@ static uint64_t unit_bytes(const KernelSet &ks, const ht_shape &s) {
   if (s.kernel != 1) return (uint64_t)ks.exec_bytes << 3;
   return ((uint64_t)ks.exec_bytes * (uint64_t)(kLanes / ks.lanes)) << (3 * s.chunk_levels);
 }
-static uint64_t groups_for(const ht_shape &s, uint64_t N) {
+static uint64_t groups_for(const KernelSet &ks, const ht_shape &s, uint64_t N) {
+  if (ks.tree) return bin_groups(N);
   return groups_of(N, s.kernel != 1 ? 1 : s.chunk_levels);
 }
 
@@ -312,7 +345,7 @@ int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t 
     func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.single_aligned[L - 1] : ks.single_unaligned[L - 1];
   }
   const int tpb = shape.threads_per_block;
-  const int occ = occupancy(func, tpb, smem);
+  const int occ = occupancy(c, func, tpb, smem);
   if (occ == 0) return set_error(HT_ERR_ARG, "launch shape does not fit the device");
   const int bps = std::min(shape.blocks_per_sm, occ);
   const uint64_t wpb = (uint64_t)tpb / 32;
@@ -362,6 +395,51 @@ int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t 
   return HT_OK;
 }
 
+// Candidate launch shapes of the three kernel families that fit the device,
+// for single strings or for batches (the warp-chunk kernel with 64-execution
+// items only, for 256-bit blocks and for the binary-tree ablation).
+static std::vector<ht_shape> tune_candidates(ht_ctx *c, bool batch) {
+  const KernelSet &ks = *c->ks;
+  const bool only_l2 = ks.lanes != kLanes || ks.tree;
+  std::vector<ht_shape> cands;
+  for (int warps : {2, 3, 4, 5, 6, 8})
+    for (int stages : {2, 3, 4, 6})
+      for (int bps : {1, 2, 3, 4}) {
+        ht_shape h = default_shape();
+        h.kernel = 0;
+        h.stages = stages;
+        h.threads_per_block = 32 * warps;
+        h.blocks_per_sm = bps;
+        if (only_l2) continue;
+        const size_t smem = stream_smem(ks, h);
+        if ((int)smem > c->smem_optin) continue;
+        if (occupancy(c, batch ? ks.stream_batch : ks.stream_single, h.threads_per_block, smem) < bps) continue;
+        cands.push_back(h);
+      }
+  for (int tpb : {128, 256})
+    for (int bps : {1, 2, 3, 4, 6, 8}) {
+      ht_shape h = default_shape();
+      h.kernel = 2;
+      h.threads_per_block = tpb;
+      h.blocks_per_sm = bps;
+      if (only_l2 || occupancy(c, batch ? ks.range_batch : ks.range_single, tpb, 0) < bps) continue;
+      cands.push_back(h);
+    }
+  for (int L : {1, 2, 3})
+    for (int tpb : {128, 256})
+      for (int bps : {1, 2, 3, 4, 6, 8}) {
+        ht_shape h = default_shape();
+        h.kernel = 1;
+        h.chunk_levels = L;
+        h.threads_per_block = tpb;
+        h.blocks_per_sm = bps;
+        const void *f = batch ? ks.batch[L - 1] : ks.single_aligned[L - 1];
+        if (!f || occupancy(c, f, tpb, 0) < bps) continue;
+        cands.push_back(h);
+      }
+  return cands;
+}
+
 }  // namespace ht
 
 using namespace ht;
@@ -405,7 +483,7 @@ int ht_ctx_create(int width, const uint64_t *seed_words, size_t n_words, ht_stre
   c->width = width;
   c->ks = ks;
   c->h_seeds.assign(seed_words, seed_words + n_words);
-  for (int i = 0; i < 65; ++i) c->shapes[i] = default_shape();
+  for (int i = 0; i < 65; ++i) c->shapes[i] = i < 64 ? default_shape(*ks, i) : default_shape();
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -497,7 +575,7 @@ int ht_hash(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest, ht_stre
   if (n_units > 0xffffffffull) return set_error(HT_ERR_TOO_LONG, "string too long for one launch");
   sp.n_items = (uint32_t)n_units;
   sp.pad = 0;
-  int rc = ensure_groups(c, groups_for(shape, sp.n_exec), s);
+  int rc = ensure_groups(c, groups_for(*c->ks, shape, sp.n_exec), s);
   if (rc) return rc;
   return launch_single(c, shape, sp, 0, n_units, digest, s);
 }
@@ -538,7 +616,7 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
   if (n_units > 0xffffffffull) return set_error(HT_ERR_TOO_LONG, "string too long for one launch");
   sp.n_items = (uint32_t)n_units;
   sp.pad = 0;
-  int rc = ensure_groups(c, groups_for(shape, sp.n_exec), s);
+  int rc = ensure_groups(c, groups_for(*c->ks, shape, sp.n_exec), s);
   if (rc) return rc;
   // slots may still be read by an earlier call's kernels on another stream
   HT_CUDA(cudaStreamSynchronize(s));
@@ -646,7 +724,7 @@ static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
     func = n.map ? ks.batch_map[shape.chunk_levels - 1] : ks.batch[shape.chunk_levels - 1];
   }
   const int tpb = shape.threads_per_block;
-  const int bps = std::max(1, std::min(shape.blocks_per_sm, occupancy(func, tpb, smem)));
+  const int bps = std::max(1, std::min(shape.blocks_per_sm, occupancy(c, func, tpb, smem)));
   n.hash.func = (void *)func;
   n.hash.gridDim = dim3((unsigned)(c->num_sms * bps));
   n.hash.blockDim = dim3(tpb);
@@ -781,6 +859,7 @@ unsigned ht_build_flags(void) { return kChecked ? HT_BUILD_CHECKED : 0u; }
 
 int ht_wait_probe(ht_ctx *c, uint64_t cycles, ht_stream_t stream) {
   if (!c || cycles == 0 || cycles > (1ull << 34)) return set_error(HT_ERR_ARG, "ht_wait_probe: bad arguments");
+  if (!c->ks->wait_probe) return set_error(HT_ERR_WIDTH, "ht_wait_probe: the binary-tree ablation has no staged kernel");
   Ctl *ctl = c->ctl;
   long long budget = (long long)cycles;
   void *args[] = {&ctl, &budget};
@@ -798,45 +877,7 @@ int ht_check_probe(ht_ctx *c, uint64_t index, uint64_t limit, ht_stream_t stream
 int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
   if (!c || len == UINT64_MAX) return set_error(HT_ERR_ARG, "ht_autotune: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
-  const KernelSet &ks = *c->ks;
-  // candidate shapes of the three kernel families that fit the device (the
-  // warp-chunk kernel with 64-execution sub-chunks only, for 256-bit blocks)
-  const bool v3 = ks.lanes != kLanes;
-  std::vector<ht_shape> cands;
-  for (int warps : {2, 3, 4, 5, 6, 8})
-    for (int stages : {2, 3, 4, 6})
-      for (int bps : {1, 2, 3, 4}) {
-        ht_shape h = default_shape();
-        h.kernel = 0;
-        h.stages = stages;
-        h.threads_per_block = 32 * warps;
-        h.blocks_per_sm = bps;
-        if (v3) continue;
-        const size_t smem = stream_smem(ks, h);
-        if ((int)smem > c->smem_optin) continue;
-        if (occupancy(ks.stream_single, h.threads_per_block, smem) < bps) continue;
-        cands.push_back(h);
-      }
-  for (int tpb : {128, 256})
-    for (int bps : {1, 2, 3, 4, 6, 8}) {
-      ht_shape h = default_shape();
-      h.kernel = 2;
-      h.threads_per_block = tpb;
-      h.blocks_per_sm = bps;
-      if (v3 || occupancy(ks.range_single, tpb, 0) < bps) continue;
-      cands.push_back(h);
-    }
-  for (int L : {2, 3})
-    for (int tpb : {128, 256})
-      for (int bps : {1, 2, 3, 4, 6, 8}) {
-        ht_shape h = default_shape();
-        h.kernel = 1;
-        h.chunk_levels = L;
-        h.threads_per_block = tpb;
-        h.blocks_per_sm = bps;
-        if (!ks.single_aligned[L - 1] || occupancy(ks.single_aligned[L - 1], tpb, 0) < bps) continue;
-        cands.push_back(h);
-      }
+  const std::vector<ht_shape> cands = tune_candidates(c, false);
   uint8_t *buf = nullptr;
   HT_CUDA(cudaMalloc((void **)&buf, std::max<uint64_t>(len, 16)));
   cudaEvent_t e0, e1;
@@ -876,6 +917,57 @@ int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
+  if (rc == HT_OK && best) *best = winner;
+  return rc;
+}
+
+int ht_autotune_batch(ht_ctx *c, const void *const *ptrs, const uint64_t *lens, size_t count,
+                      uint64_t *digests, ht_stream_t stream, ht_shape *best) {
+  if (!c || count == 0 || !ptrs || !lens || !digests)
+    return set_error(HT_ERR_ARG, "ht_autotune_batch: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::vector<ht_shape> cands = tune_candidates(c, true);
+  cudaEvent_t e0, e1;
+  HT_CUDA(cudaEventCreate(&e0));
+  HT_CUDA(cudaEventCreate(&e1));
+  const ht_shape saved = c->shapes[64];
+  ht_shape winner = saved;
+  float best_ms = 1e30f;
+  int rc = HT_OK;
+  bool any = false;
+  for (size_t i = 0; i < cands.size() && rc == HT_OK; ++i) {
+    c->shapes[64] = cands[i];
+    rc = ht_hash_batch(c, ptrs, lens, count, digests, stream);  // warm-up (builds the graph)
+    if (rc) break;
+    const int st = read_status(c->ctl, s);
+    if (st == HT_ERR_TOO_LONG) continue;  // this chunk height needs more group slots
+    if (st) {
+      rc = st;
+      break;
+    }
+    float times[3] = {0, 0, 0};
+    for (int r = 0; r < 3 && rc == HT_OK; ++r) {
+      cudaEventRecord(e0, s);
+      rc = ht_hash_batch(c, ptrs, lens, count, digests, stream);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&times[r], e0, e1);
+    }
+    if (rc) break;
+    std::sort(times, times + 3);
+    any = true;
+    if (times[1] < best_ms) {
+      best_ms = times[1];
+      winner = cands[i];
+    }
+  }
+  if (rc == HT_OK && !any) rc = set_error(HT_ERR_TOO_LONG, "ht_autotune_batch: the batch fits no shape's scratch");
+  c->shapes[64] = (rc == HT_OK) ? winner : saved;
+  // the digests of the winning shape (every shape gives the same digests)
+  if (rc == HT_OK) rc = ht_hash_batch(c, ptrs, lens, count, digests, stream);
+  if (rc == HT_OK) rc = read_status(c->ctl, s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   if (rc == HT_OK && best) *best = winner;
   return rc;
 }

@@ -170,7 +170,7 @@ extern "C" {
 int ht_inc_create(ht_ctx *c, ht_inc **out) {
   if (!c || !out) return set_error(HT_ERR_ARG, "ht_inc_create: NULL argument");
   *out = nullptr;
-  if (c->ks->lanes != kLanes)
+  if (c->ks->lanes != kLanes || c->ks->tree)
     return set_error(HT_ERR_WIDTH, "ht_inc_create: incremental hashing takes 512-bit blocks");
   ht_inc *h = new ht_inc;
   h->ctx = c;

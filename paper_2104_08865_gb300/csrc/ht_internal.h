@@ -136,6 +136,11 @@ struct KernelSet {
   // only the warp-chunk kernels with 64-execution sub-chunks (index L = 2)
   // and the multi-block planner; its other entries are null
   int lanes;
+  // tree: 0 for the paper's T-hat (8-ary, pending roots, final NH), 1 for the
+  // binary-tree ablation (Eq. algebraic-badger over all EHC outputs; its set
+  // holds the single and batch kernels with 64-execution items (index L = 2)
+  // and the multi-block planner; level keys at off_T + 64 t + h)
+  int tree;
 };
 
 const KernelSet &kernels_w16();
@@ -147,5 +152,10 @@ const KernelSet &kernels_w16_v3();
 const KernelSet &kernels_w24_v3();
 const KernelSet &kernels_w32_v3();
 const KernelSet &kernels_w40_v3();
+// the same widths under the binary-tree ablation
+const KernelSet &kernels_w16_bin();
+const KernelSet &kernels_w24_bin();
+const KernelSet &kernels_w32_bin();
+const KernelSet &kernels_w40_bin();
 
 }  // namespace ht

@@ -249,12 +249,14 @@ __device__ __forceinline__ uint64_t final_key(const KParams &P, int t, int lvl, 
 // ---- the finaliser: pending-root sum + Toeplitz tail (Section 6.1) ----------
 
 // The Toeplitz tail NH of the string, length word included (Section 6.1, and
-// reading 9), summed over the warp: every lane gets the k sums.
-template <int W, int B = kLanes>
+// reading 9), summed over the warp: every lane gets the k sums.  BIN: the
+// tail keys sit where the binary-tree ablation's seed layout puts them.
+template <int W, int B = kLanes, bool BIN = false>
 __device__ __forceinline__ void tail_sum(const KParams &P, const StrPlan &sp, int ln,
                                          uint64_t (&sum)[Spec<W>::k]) {
   constexpr int k = Spec<W>::k;
   constexpr int XB = Dims<W, B>::exec_bytes;
+  constexpr int ROFF = BIN ? BinDims<W>::off_R : Dims<W, B>::off_R;
   const uint64_t tstart = sp.n_exec * (uint64_t)XB;
   const uint64_t tlen = sp.len - tstart;  // < B
   const uint32_t M = (uint32_t)((tlen + 7) / 8);
@@ -273,13 +275,13 @@ __device__ __forceinline__ void tail_sum(const KParams &P, const StrPlan &sp, in
 #pragma unroll
     for (int t = 0; t < k; ++t)
       if (HT_IN_RANGE(P, kChkSeedR, t + m, (B * Dims<W, B>::dw + k)))
-        sum[t] += nh64(word, __ldg(P.seeds + Dims<W, B>::off_R + t + m));
+        sum[t] += nh64(word, __ldg(P.seeds + ROFF + t + m));
   }
 #pragma unroll
   for (int t = 0; t < k; ++t) sum[t] = warp_sum(sum[t]);
 }
 
-template <int W, int B = kLanes>
+template <int W, int B = kLanes, bool BIN = false>
 __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx, int ln) {
   constexpr int k = Spec<W>::k;
   __threadfence();
@@ -288,7 +290,7 @@ __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx
 #pragma unroll
   for (int t = 0; t < k; ++t) acc[t] = str_ok ? ld_cg(P.scr.str_acc + (uint64_t)sidx * k + t) : 0;
   uint64_t sum[k];
-  tail_sum<W, B>(P, sp, ln, sum);
+  tail_sum<W, B, BIN>(P, sp, ln, sum);
   if (ln == 0 && str_ok) {
     const bool dig_ok = HT_IN_RANGE(P, kChkDigest, sidx, P.count);
 #pragma unroll
@@ -303,12 +305,12 @@ __device__ void finish_string(const KParams &P, const StrPlan &sp, unsigned sidx
 // A string with a single work item: its warp holds the whole final-NH sum
 // (pend, spread over the lanes), so it writes the digest without the
 // string's scratch sum and completion count.
-template <int W, int B = kLanes>
+template <int W, int B = kLanes, bool BIN = false>
 __device__ void finish_local(const KParams &P, const StrPlan &sp, unsigned sidx,
                              uint64_t (&pend)[Spec<W>::k], int ln) {
   constexpr int k = Spec<W>::k;
   uint64_t sum[k];
-  tail_sum<W, B>(P, sp, ln, sum);
+  tail_sum<W, B, BIN>(P, sp, ln, sum);
 #pragma unroll
   for (int t = 0; t < k; ++t) sum[t] += warp_sum(pend[t]);
   if (ln == 0 && HT_IN_RANGE(P, kChkDigest, sidx, P.count))
@@ -1078,7 +1080,8 @@ __device__ __forceinline__ unsigned long long plan_groups(uint64_t N) {
 
 // 1: the work items and tree-group slots of every string of a tile, the
 // tile's totals and whether it holds a string that is not 16-byte aligned.
-template <int W, int L, int B = kLanes>
+// BIN: tree-group slots of the binary-tree ablation.
+template <int W, int L, int B = kLanes, bool BIN = false>
 __global__ void __launch_bounds__(1024) plan_tiles_kernel(const PlanArgs A) {
   constexpr uint64_t XB = Dims<W, B>::exec_bytes;
   __shared__ unsigned long long sh[32];
@@ -1088,7 +1091,7 @@ __global__ void __launch_bounds__(1024) plan_tiles_kernel(const PlanArgs A) {
   if (i < A.count) {
     const uint64_t N = A.lens[i] / XB;
     it = plan_items<L, B>(N);
-    gr = plan_groups<L>(N);
+    gr = BIN ? bin_groups(N) : plan_groups<L>(N);
     un = (((uintptr_t)A.ptrs[i]) & 15u) != 0;
   }
   const int any_un = __syncthreads_or(un);
@@ -1136,7 +1139,7 @@ __global__ void __launch_bounds__(1024) plan_totals_kernel(const PlanArgs A) {
 }
 
 // 3: every string's plan, its first item and its first group slot.
-template <int W, int L, int B = kLanes>
+template <int W, int L, int B = kLanes, bool BIN = false>
 __global__ void __launch_bounds__(1024) plan_write_kernel(const PlanArgs A) {
   constexpr uint64_t XB = Dims<W, B>::exec_bytes;
   __shared__ unsigned long long sh[32];
@@ -1147,7 +1150,7 @@ __global__ void __launch_bounds__(1024) plan_write_kernel(const PlanArgs A) {
     len = A.lens[i];
     N = len / XB;
     it = plan_items<L, B>(N);
-    gr = plan_groups<L>(N);
+    gr = BIN ? bin_groups(N) : plan_groups<L>(N);
   }
   unsigned long long ti, tg;
   const unsigned long long ei = block_scan(it, sh, &ti) + A.tile_items[blockIdx.x];

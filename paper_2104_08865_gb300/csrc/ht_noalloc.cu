@@ -79,7 +79,7 @@ extern "C" int ht_hash_noalloc(int width_bytes, const uint64_t *seed_words_host,
                                const void *data_dev, uint64_t len, uint64_t *digest_dev,
                                ht_stream_t stream) {
   const ht::KernelSet *ks = ht::kernel_set(width_bytes);
-  if (!ks || ks->lanes != ht::kLanes) return ht::set_error(HT_ERR_WIDTH, "unsupported width %d", width_bytes);
+  if (!ks || ks->lanes != ht::kLanes || ks->tree) return ht::set_error(HT_ERR_WIDTH, "unsupported width %d", width_bytes);
   if (!seed_words_host || n_words != (size_t)ks->n_seed || !digest_dev || (len && !data_dev))
     return ht::set_error(HT_ERR_ARG, "ht_hash_noalloc: bad arguments (need %d seed words)", ks->n_seed);
   const uint64_t N = len / (uint64_t)ks->exec_bytes;

@@ -66,16 +66,17 @@ using namespace ht;
 extern "C" {
 
 uint64_t ht_part_granule(ht_ctx *c) {
-  return c && c->ks->lanes == kLanes ? (uint64_t)c->ks->exec_bytes << (3 * kPartLevels) : 0;
+  return c && c->ks->lanes == kLanes && !c->ks->tree ? (uint64_t)c->ks->exec_bytes << (3 * kPartLevels) : 0;
 }
 
 size_t ht_part_state_words(ht_ctx *c, uint64_t total_len) {
-  return c && c->ks->lanes == kLanes ? (size_t)part_layout(*c->ks, total_len / (uint64_t)c->ks->exec_bytes).words : 0;
+  return c && c->ks->lanes == kLanes && !c->ks->tree ? (size_t)part_layout(*c->ks, total_len / (uint64_t)c->ks->exec_bytes).words : 0;
 }
 
 int ht_part_begin(ht_ctx *c, uint64_t total_len, void *state_dev, size_t words, ht_stream_t stream) {
   if (!c) return set_error(HT_ERR_ARG, "ht_part_begin: NULL context");
-  if (c->ks->lanes != kLanes) return set_error(HT_ERR_WIDTH, "ht_part_begin: parts take 512-bit blocks");
+  if (c->ks->lanes != kLanes || c->ks->tree)
+    return set_error(HT_ERR_WIDTH, "ht_part_begin: parts take 512-bit blocks and the default tree");
   const PartLayout L = part_layout(*c->ks, total_len / (uint64_t)c->ks->exec_bytes);
   cudaStream_t s = (cudaStream_t)stream;
   if (state_dev) {

@@ -291,6 +291,7 @@ KernelSet make_kernel_set() {
   ks.off_R = Dims<W>::off_R;
   ks.ew = Dims<W>::ew;
   ks.lanes = kLanes;
+  ks.tree = 0;
   return ks;
 }
 

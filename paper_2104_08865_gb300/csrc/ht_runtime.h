@@ -63,6 +63,15 @@ struct ht_ctx {
   bool part_open = false;
   bool part_owned = false;  // part_buf allocated by the library
   std::atomic<uint64_t> launches{0};
+  // blocks per SM of (kernel, threads per block, dynamic shared memory),
+  // queried once per context (the query costs more than a small launch)
+  struct Occ {
+    const void *func;
+    int tpb;
+    size_t smem;
+    int blocks;
+  };
+  std::vector<Occ> occ_cache;
 };
 
 namespace ht {

@@ -405,7 +405,9 @@ int make_server(ht_server *S, ht_ctx *ctx, uint64_t budget, const ht_server_opts
     if (rc) return rc;
     rc = ht_ctx_reserve(sl.ctx, budget, o.max_batch);
     if (rc) return rc;
-    sl.ctx->shapes[64] = ctx->shapes[64];
+    // every length bucket's launch shape (a lone request is a single-string
+    // launch) and the batch shape
+    for (int b = 0; b < 65; ++b) sl.ctx->shapes[b] = ctx->shapes[b];
     e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&sl.h_ptrs, o.max_batch * sizeof(void *));

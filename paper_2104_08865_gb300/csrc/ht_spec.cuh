@@ -120,4 +120,26 @@ struct Dims {
   static constexpr int n_seed = off_R + B * dw + k;
 };
 
+// Seed layout of the binary-tree ablation (Badger's approach, Section 5.2):
+// the EHC keys E (e*w words), then 64 level keys per tree (key h of tree t at
+// off_T + 64 t + h; a binary node spans fewer than 2^64 leaves), then the
+// Toeplitz tail keys; no final-NH region.  512-bit blocks.
+constexpr int kBinLevels = 64;
+template <int W>
+struct BinDims {
+  static constexpr int k = Spec<W>::k;
+  static constexpr int off_T = Dims<W>::ew;
+  static constexpr int off_R = off_T + k * kBinLevels;
+  static constexpr int n_seed = off_R + kLanes * Dims<W>::dw + k;
+};
+
+// Tree-group slots of a string of N executions under the binary-tree
+// ablation: one per pair of complete nodes at every height h >= 9 (above a
+// 64-execution work item), where height h holds N >> (h - 3) complete nodes.
+__host__ __device__ inline unsigned long long bin_groups(uint64_t N) {
+  unsigned long long g = 0;
+  for (int j = 6; j < 64; ++j) g += (N >> j) >> 1;
+  return g;
+}
+
 }  // namespace ht

@@ -74,8 +74,24 @@ def test_256_bit_blocks_rejected_where_unsupported(built):
     with pytest.raises(abi.HalftimeError) as e:
         abi.ht_hash_noalloc(code, abi.ht_seed_expand(7, code), 0, 0, 0)
     assert e.value.code == abi.HT_ERR_WIDTH
-    assert abi.ht_seed_words(24 | 0x200) == 0
+    assert abi.ht_seed_words(24 | 0x400) == 0
     assert abi.ht_seed_words(abi.HT_BLOCK_256) == 0
+    assert abi.ht_seed_words(24 | abi.HT_BLOCK_256 | abi.HT_TREE_BINARY) == 0
+    assert abi.ht_seed_words(abi.HT_TREE_BINARY) == 0
+
+
+@pytest.mark.parametrize("width", [16, 24, 32, 40])
+def test_seed_expansion_binary_tree_matches_oracle(built, width):
+    """The binary-tree ablation's seed layout (E, 64 level keys per output
+    word, R) has the oracle's size and words; the allocation-free call
+    refuses the ablation before any CUDA work."""
+    from paper_2104_08865_gb300 import abi
+    code = width | abi.HT_TREE_BINARY
+    assert abi.ht_seed_words(code) == oracle.seed_words_badger(width)
+    assert np.array_equal(abi.ht_seed_expand(7, code), oracle.seed_expand(7, oracle.seed_words_badger(width)))
+    with pytest.raises(abi.HalftimeError) as e:
+        abi.ht_hash_noalloc(code, abi.ht_seed_expand(7, code), 0, 0, 0)
+    assert e.value.code == abi.HT_ERR_WIDTH
 
 
 def test_argument_errors(built):
