@@ -12,11 +12,18 @@ the four hashes (4 GiB hashed).  The input is larger than L2 (1 GiB vs
           are inside the timed region.
   roofline  the dominant kernel (the slowest width) against the measured HBM
           copy bandwidth; algorithmic bytes = 2^30 read per launch.
-  cpu_baseline  the CPU oracle on the same bytes (one thread per width).
+  cpu_baseline  the CPU oracle on the machine's host cores: all cores at once
+          (independent 64 MiB pieces of the string), one thread, and the
+          whole string at every width (its digests checked against the GPU's).
   blocks_256  the same string and widths with 256-bit blocks (b = 4 words).
+  tree_ablation  the same string and widths under the binary-tree ablation
+          (Badger's approach) against the paper's tree.
+  size_sweep  per-launch time of 1..256 MiB strings (widths 24, 40).
+  batch   the 50,000-string batch: default and autotuned batch shape, the
+          strings below one chunk and the rest, and one launch per string.
 
 `--impl reference` times the CPU oracle instead (the reference arm): each step
-hashes a bounded sample (the first 64 MiB of the string at each width).
+hashes the whole string at each width, one oracle thread per width.
 """
 from __future__ import annotations
 
@@ -197,30 +204,37 @@ def _workload(nbytes: int) -> str:
             "16/24/32/40 (seed %d) per step" % (nbytes >> 20, SEED_DATA, SEED_KEY))
 
 
+def _config(nbytes: int) -> dict:
+    """The workload both arms name in `config`."""
+    return {"workload": _workload(nbytes), "bytes_per_step": len(WIDTHS) * nbytes,
+            "l2": "inputs larger than L2 (no flush)"}
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle on the same workload, the whole
+    string at each of the four widths per step, one oracle thread per width
+    (the oracle hashes one string serially)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    import numpy as np
-
     from paper_2104_08865_gb300 import inputs
-    sample = 64 << 20
-    data = inputs.stream_bytes(SEED_DATA, 0, sample)
+    nbytes = args.bytes
+    data = inputs.stream_bytes(SEED_DATA, 0, nbytes)
     for _ in range(args.warmup):
-        _oracle_gbs(data, sample)
+        _oracle_gbs(data, nbytes)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _oracle_gbs(data, sample)
+        _oracle_gbs(data, nbytes)
     dt = time.perf_counter() - t0
-    gbs = args.steps * len(WIDTHS) * sample / dt / 1e9
-    desc = ("each step: the first 64 MiB of the string at each of the four widths (a bounded "
-            "sample of the workload; GB/s over the bytes hashed), one oracle thread per width")
+    gbs = args.steps * len(WIDTHS) * nbytes / dt / 1e9
+    desc = ("each step: the whole %d MiB string at each of the four widths, one oracle thread "
+            "per width" % (nbytes >> 20))
     line = {
         "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1000 * dt / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": _workload(args.bytes), "bytes_per_step": len(WIDTHS) * args.bytes},
+        "config": _config(nbytes),
         "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": len(WIDTHS),
                          "host_cores": os.cpu_count(), "kind": "oracle", "sample": desc},
         "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
@@ -228,6 +242,28 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _oracle_threads_gbs(data_np, piece: int, threads: int):
+    """`threads` oracle threads at once, thread i hashing its own piece of
+    `piece` bytes of the string (pieces wrap around the string) at width
+    WIDTHS[i % 4]: the host's throughput over independent strings."""
+    import oracle
+    seeds = {w: oracle.seed_expand(SEED_KEY, oracle.seed_words(w)) for w in WIDTHS}
+    n = len(data_np)
+
+    def run(i):
+        o = (i * piece) % max(1, n - piece + 1)
+        oracle.hash_bytes(WIDTHS[i % 4], seeds[WIDTHS[i % 4]], data_np[o:o + piece])
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=run, args=(i,)) for i in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    dt = time.perf_counter() - t0
+    return threads * piece / dt / 1e9
 
 
 def _aligned_offsets(lens, align=256):
@@ -258,25 +294,47 @@ def run_batch(args, dev, stream):
     lt = torch.tensor(lens, dtype=torch.int64, device=dev)
     h = Hasher(24, seed_words=abi.ht_seed_expand(SEED_KEY, 24))
     out = torch.empty((count, 3), dtype=torch.int64, device=dev)
-    for _ in range(3):
-        abi.ht_hash_batch(h.ctx, ptrs, lt, count, out, stream)
-    torch.cuda.synchronize()
-    h.status()
     reps = 10
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = h.launches()
-    e0.record(stream)
-    for _ in range(reps):
-        abi.ht_hash_batch(h.ctx, ptrs, lt, count, out, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_batch = shard.max_over_ranks(e0.elapsed_time(e1) / reps, dev)
-    launches_batch = (h.launches() - l0) // reps
+
+    def timed(p, l, n, o):
+        for _ in range(3):
+            abi.ht_hash_batch(h.ctx, p, l, n, o, stream)
+        torch.cuda.synchronize()
+        h.status()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = h.launches()
+        e0.record(stream)
+        for _ in range(reps):
+            abi.ht_hash_batch(h.ctx, p, l, n, o, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, (h.launches() - l0) // reps
+
+    # the default batch shape, then the batch autotuner's pick (set-up, untimed)
+    ms_default, _ = timed(ptrs, lt, count, out)
+    default_shape = abi.ht_get_shape(h.ctx, 2**64 - 1)
+    tuned_shape = abi.ht_autotune_batch(h.ctx, ptrs, lt, count, out, stream)
+    ms_batch, launches_batch = timed(ptrs, lt, count, out)
+    ms_batch = shard.max_over_ranks(ms_batch, dev)
+    # strings below one 64-execution chunk and the rest, each as a batch
+    chunk = 64 * 1344
+    classes = {}
+    for name, sel in (("under_one_chunk", lens < chunk), ("one_chunk_or_more", lens >= chunk)):
+        idx = torch.tensor(np.nonzero(sel)[0], dtype=torch.int64, device=dev)
+        m = int(idx.numel())
+        if m == 0:
+            continue
+        o2 = torch.empty((m, 3), dtype=torch.int64, device=dev)
+        ms_c, _ = timed(ptrs[idx].contiguous(), lt[idx].contiguous(), m, o2)
+        b = int(lens[sel].sum())
+        classes[name] = {"strings": m, "gb": round(b / 1e9, 3), "ms": round(ms_c, 3),
+                         "gbs": round(b / ms_c / 1e6, 1)}
     nbytes = int(all_lens.sum())
     naive = torch.empty_like(out)
     hp = (buf.data_ptr() + offs).astype(np.uint64)
     h.hash_batch_naive(hp, lens, naive)  # warm-up
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     h.hash_batch_naive(hp, lens, naive)
     e1.record(stream)
@@ -287,7 +345,9 @@ def run_batch(args, dev, stream):
     return {"workload": "%d strings, log-uniform 64 B..1 MiB, %.2f GB, width 24%s" % (
                 args.batch_strings, nbytes / 1e9, "" if ws == 1 else ", sharded by bytes over %d ranks" % ws),
             "batch_gbs": round(nbytes / ms_batch / 1e6, 1), "batch_ms": round(ms_batch, 3),
-            "batch_launches": launches_batch,
+            "batch_launches": launches_batch, "tuned_shape": tuned_shape,
+            "default_shape_gbs": round(nbytes / ms_default / 1e6, 1), "default_shape": default_shape,
+            "classes": classes,
             "naive_gbs": round(nbytes / ms_naive / 1e6, 1), "naive_ms": round(ms_naive, 3),
             "naive_launches": args.batch_strings, "speedup": round(ms_naive / ms_batch, 2),
             "digests_equal": same}
@@ -472,6 +532,84 @@ def run_v3(args, dev, stream, data):
     for h in hs.values():
         h.close()
     return res
+
+
+def run_tree_ablation(args, dev, stream, data):
+    """The binary-tree ablation (width | HT_TREE_BINARY: Badger's approach,
+    Eq. algebraic-badger over all EHC outputs, no final NH) against the
+    paper's tree on the benchmark string: each width's launch timed alone
+    with CUDA events, default launch shapes, both trees."""
+    import numpy as np
+    import torch
+
+    from paper_2104_08865_gb300 import Hasher, abi
+    nbytes = args.bytes
+    res = {"workload": _workload(nbytes).replace("hashed at widths", "tree T-hat vs binary tree, widths"),
+           "per_width": {}}
+    reps = 20
+    for w in WIDTHS:
+        row = {}
+        for name, code in (("t_hat", w), ("binary", w | abi.HT_TREE_BINARY)):
+            h = Hasher(code, seed_words=abi.ht_seed_expand(SEED_KEY, code))
+            out = torch.empty(w // 8, dtype=torch.int64, device=dev)
+            for _ in range(3):
+                abi.ht_hash(h.ctx, data.data_ptr(), nbytes, out.data_ptr(), stream)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a, b in evs:
+                a.record(stream)
+                abi.ht_hash(h.ctx, data.data_ptr(), nbytes, out.data_ptr(), stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            h.status()
+            us = statistics.mean(a.elapsed_time(b) for a, b in evs) * 1000
+            row[name] = {"us": round(us, 2), "gbs": round(nbytes / us / 1e3, 1),
+                         "digest": ["%016x" % v for v in out.cpu().numpy().view(np.uint64)]}
+            h.close()
+        row["binary_over_t_hat_time"] = round(row["binary"]["us"] / row["t_hat"]["us"], 3)
+        res["per_width"][str(w)] = row
+    return res
+
+
+def run_size_sweep_leg(args, dev, stream, data):
+    """Per-launch time of single strings of 1 to 256 MiB (widths 24 and 40,
+    the default launch shape of each length): back-to-back launches timed
+    with CUDA events (the fixed cost of a launch against its bytes), and the
+    median of 20 lone launches (events around one launch, synchronised)."""
+    import torch
+
+    from paper_2104_08865_gb300 import Hasher, abi
+    rows = []
+    for w in (24, 40):
+        h = Hasher(w, seed_words=abi.ht_seed_expand(SEED_KEY, w))
+        out = torch.empty(w // 8, dtype=torch.int64, device=dev)
+        for mib in (1, 4, 16, 64, 256):
+            n = mib << 20
+            for _ in range(3):
+                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), stream)
+            reps = max(10, min(200, (2 * GIB) // n))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1000 / reps
+            lone = []
+            for _ in range(20):
+                e0.record(stream)
+                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                lone.append(e0.elapsed_time(e1) * 1000)
+            shape = abi.ht_get_shape(h.ctx, n)
+            rows.append({"width": w, "mib": mib, "us": round(us, 2), "gbs": round(n / us / 1e3, 1),
+                         "lone_us": round(statistics.median(lone), 2),
+                         "chunk_levels": shape["chunk_levels"]})
+        h.status()
+        h.close()
+    return {"note": "per-launch time, default shape per length; us = back-to-back mean, "
+                    "lone_us = median of one launch between events", "rows": rows}
 
 
 def run_serving(args, dev, stream):
@@ -669,17 +807,30 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu:
         host_np = data.cpu().numpy()
         sample = min(nbytes, args.cpu_bytes)
-        gbs, dt, ref = _oracle_gbs(host_np, sample)
+        # the whole string at every width, one thread per width: the digests
+        # must equal the GPU's
+        gbs4, dt, ref = _oracle_gbs(host_np, sample)
         match = None
         if sample == nbytes:
             match = all(np.array_equal(np.asarray(digests[w], dtype=np.uint64), ref[w]) for w in WIDTHS)
-        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": len(WIDTHS), "kind": "oracle",
-               "host_cores": os.cpu_count(),
-               "sample": "first %d MiB of the string at each of the four widths, one oracle thread "
-                         "per width (%.1f s)" % (sample >> 20, dt),
+        cores = os.cpu_count() or 1
+        piece = min(64 << 20, nbytes)
+        single = _oracle_threads_gbs(host_np, piece, 1)
+        allc = _oracle_threads_gbs(host_np, piece, cores)
+        cpu = {"value": round(allc, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "host_cores": cores,
+               "sample": "all host cores: %d oracle threads at once, each hashing its own %d MiB piece "
+                         "of the string (widths in turn)" % (cores, piece >> 20),
+               "single_thread_gbs": round(single, 4),
+               "single_thread_sample": "one oracle thread, a %d MiB piece at width 16" % (piece >> 20),
+               "four_widths_gbs": round(gbs4, 4),
+               "four_widths_sample": "the whole %d MiB string at each width, one thread per width "
+                                     "(%.1f s)" % (sample >> 20, dt),
                "digests_match_gpu": match}
 
     v3 = run_v3(args, dev, stream, data) if (rank == 0 and not args.no_v3) else None
+    ablation = run_tree_ablation(args, dev, stream, data) if (rank == 0 and not args.no_ablation) else None
+    sweep = run_size_sweep_leg(args, dev, stream, data) if (rank == 0 and not args.no_sweep) else None
     batch = run_batch(args, dev, stream) if not args.no_batch else None
     incremental = (run_incremental(args, dev, stream, data, digests[24])
                    if (rank == 0 and not args.no_inc) else None)
@@ -692,10 +843,8 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": _workload(nbytes),
-                       "bytes_per_step": len(WIDTHS) * nbytes,
-                       "l2": "inputs larger than L2 (no flush)",
-                       "launches": "back to back on one stream" + (
+            "config": _config(nbytes),
+            "timing": {"launches": "back to back on one stream" + (
                            "" if args.no_overlap else ", overlapping (programmatic dependent launch)"),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "per_width_gbs": {str(w): round(nbytes / (per_w[w] / 1e3) / 1e9, 2) for w in WIDTHS},
@@ -708,7 +857,7 @@ def run_gpu(args):
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": ck,
             "shapes": shapes,
             "batch": batch, "incremental": incremental, "dedup": dedup, "serving": serving,
-            "blocks_256": v3,
+            "blocks_256": v3, "tree_ablation": ablation, "size_sweep": sweep,
             "digests": {str(w): ["%016x" % v for v in digests[w]] for w in WIDTHS},
         }
         print(json.dumps(line), flush=True)
@@ -740,6 +889,8 @@ def main():
     ap.add_argument("--no-inc", action="store_true", help="skip the incremental-hashing leg")
     ap.add_argument("--no-dedup", action="store_true", help="skip the deduplication leg")
     ap.add_argument("--no-v3", action="store_true", help="skip the 256-bit-block leg")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the binary-tree ablation leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-size launch-time leg")
     ap.add_argument("--batch-strings", type=int, default=50_000)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
