@@ -155,12 +155,15 @@ def run_size_sweep(args):
         h = Hasher(w, seed_words=abi.ht_seed_expand(SEED_KEY, w))
         for n in [1 << 20, 16 << 20, 64 << 20, 256 << 20, 512 << 20, GIB, 2 * GIB, 4 * GIB]:
             reps = max(5, min(200, (8 * GIB) // n))
-            for _ in range(3):
-                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), s)
+            # successive launches read pieces at least 384 MiB apart (from HBM)
+            copies = min(maxn // n, max(1, (384 << 20) // n + 1))
+            at = [data.data_ptr() + (i % copies) * n for i in range(reps + 3)]
+            for i in range(3):
+                abi.ht_hash(h.ctx, at[i], n, out.data_ptr(), s)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
-            for _ in range(reps):
-                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), s)
+            for i in range(reps):
+                abi.ht_hash(h.ctx, at[3 + i], n, out.data_ptr(), s)
             e1.record(s)
             torch.cuda.synchronize()
             us = e0.elapsed_time(e1) * 1000 / reps
@@ -574,7 +577,10 @@ def run_size_sweep_leg(args, dev, stream, data):
     """Per-launch time of single strings of 1 to 256 MiB (widths 24 and 40,
     the default launch shape of each length): back-to-back launches timed
     with CUDA events (the fixed cost of a launch against its bytes), and the
-    median of 20 lone launches (events around one launch, synchronised)."""
+    median of 20 lone launches (events around one launch, synchronised).
+    Successive launches hash successive n-byte pieces of the 1 GiB string,
+    at least 384 MiB apart before one is read again, so every launch reads
+    from HBM, not from the L2 cache."""
     import torch
 
     from paper_2104_08865_gb300 import Hasher, abi
@@ -584,27 +590,30 @@ def run_size_sweep_leg(args, dev, stream, data):
         out = torch.empty(w // 8, dtype=torch.int64, device=dev)
         for mib in (1, 4, 16, 64, 256):
             n = mib << 20
-            for _ in range(3):
-                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), stream)
+            copies = min(data.numel() // n, max(1, (384 << 20) // n + 1))
+            at = [data.data_ptr() + (i % copies) * n for i in range(400)]
+            for i in range(3):
+                abi.ht_hash(h.ctx, at[i], n, out.data_ptr(), stream)
             reps = max(10, min(200, (2 * GIB) // n))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            for _ in range(reps):
-                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), stream)
+            for i in range(reps):
+                abi.ht_hash(h.ctx, at[i], n, out.data_ptr(), stream)
             e1.record(stream)
             torch.cuda.synchronize()
             us = e0.elapsed_time(e1) * 1000 / reps
             lone = []
-            for _ in range(20):
+            for i in range(20):
                 e0.record(stream)
-                abi.ht_hash(h.ctx, data.data_ptr(), n, out.data_ptr(), stream)
+                abi.ht_hash(h.ctx, at[200 + i], n, out.data_ptr(), stream)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 lone.append(e0.elapsed_time(e1) * 1000)
             shape = abi.ht_get_shape(h.ctx, n)
             rows.append({"width": w, "mib": mib, "us": round(us, 2), "gbs": round(n / us / 1e3, 1),
                          "lone_us": round(statistics.median(lone), 2),
+                         "kernel": {1: "warp-chunk", 3: "block-chunk"}.get(shape["kernel"], shape["kernel"]),
                          "chunk_levels": shape["chunk_levels"]})
         h.status()
         h.close()

@@ -150,7 +150,10 @@ int ht_ctx_reserve(ht_ctx *ctx, uint64_t max_total_bytes, size_t max_strings);
  * device exceeded the reserved scratch (that batch's digests were not
  * written), HT_ERR_DEVICE when a bounded wait ran out or when the checked
  * build skipped an out-of-range access (the message names the buffer and
- * the index), or HT_ERR_CUDA. */
+ * the index), or HT_ERR_CUDA.  After HT_ERR_DEVICE the digests of the calls
+ * since the last status check are not valid, and the context's scratch
+ * (tree groups, string sums, counters) is cleared before the call returns,
+ * so the context hashes correctly again. */
 int ht_ctx_status(ht_ctx *ctx, ht_stream_t stream);
 
 /* Runs, on `stream`, the bounded wait that the stream kernel uses for its
@@ -438,15 +441,19 @@ int ht_table_status(ht_table *t, ht_stream_t stream);
  * present on every GPU that loads the library until the process exits.  It
  * calls no cudaMalloc, cudaFree or other allocating routine.
  *   - seed_words_host: the n_words = ht_seed_words(width_bytes) seed words on
- *     the host; they are copied into the array on `stream`.
+ *     the host; they are copied into the array on `stream` (a copy from
+ *     pageable memory is taken before the call returns; from pinned memory
+ *     the words must stay unchanged until the stream reaches the copy).
  *   - data_dev / len / digest_dev / stream: as ht_hash (k digest words).
  *   - Limit: the tree scratch of the array holds 63107 / 42501 / 32039 /
  *     25710 node groups for widths 16 / 24 / 32 / 40, enough for strings of
  *     about 32 / 25 / 19 / 11 GB; longer strings return HT_ERR_TOO_LONG with
  *     no GPU work.
  *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture.
+ *     per device, with that device current) and loads the kernels this call
+ *     launches for every width (with lazy module loading they would
+ *     otherwise load, with driver-side allocations, at their first launch);
+ *     make that first call before any stream capture.
  *   - Every call shares the one array and clears the parts it uses at the
  *     start, so calls that overlap on the GPU (other streams, other host
  *     threads) race and give wrong digests: order them.
@@ -477,8 +484,10 @@ typedef struct ht_shape {
   int blocks_per_sm;     /* 1 .. 32; clamped to the occupancy limit */
 } ht_shape;
 
-/* Times every candidate shape on a device buffer of `len` bytes (allocated
- * and freed inside the call) and stores the fastest in the bucket of len;
+/* Times every candidate shape on `len`-byte strings in a device buffer
+ * allocated and freed inside the call (at least 384 MiB, so that short
+ * strings are timed from HBM, not from the L2 cache: each launch takes the
+ * next copy) and stores the fastest in the bucket of len;
  * writes it to *best if best is not NULL.  Synchronous.  Errors: HT_ERR_ARG,
  * HT_ERR_NOMEM, HT_ERR_CUDA. */
 int ht_autotune(ht_ctx *ctx, uint64_t len, ht_stream_t stream, ht_shape *best);

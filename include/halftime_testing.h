@@ -26,6 +26,16 @@ int ht_server_create_fake(int width_bytes, uint64_t budget_bytes,
                           const ht_server_opts *opts, uint64_t batch_delay_us,
                           int64_t fail_batch, ht_server **out);
 
+/* Sets the limit, in SM clock cycles, of the stream kernel's waits for its
+ * shared-memory stages on this context (0: the default, about a second;
+ * at most 2^34).  The wait that lets a warp's copies in flight land before
+ * it exits keeps the default.  With a limit of a few cycles the first stage
+ * wait runs out while its copy is still in flight: the kernel reports
+ * HT_ERR_DEVICE through ht_ctx_status, which also clears the context's
+ * scratch, and the context hashes correctly afterwards.  Errors:
+ * HT_ERR_ARG. */
+int ht_testing_set_wait_cycles(ht_ctx *ctx, uint64_t cycles);
+
 #ifdef __cplusplus
 }
 #endif

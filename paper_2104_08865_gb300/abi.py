@@ -129,6 +129,7 @@ _PROTOS = {
     "ht_build_flags": (ctypes.c_uint, []),
     "ht_check_probe": (_int, [_vp, _u64, _u64, _vp]),
     "ht_wait_probe": (_int, [_vp, _u64, _vp]),
+    "ht_testing_set_wait_cycles": (_int, [_vp, _u64]),
     "ht_inc_status": (_int, [_vp, _vp]),
     "ht_server_create": (_int, [_vp, _u64, ctypes.POINTER(ht_server_opts), ctypes.POINTER(_vp)]),
     "ht_server_create_fake": (_int, [_int, _u64, ctypes.POINTER(ht_server_opts), _u64,
@@ -450,6 +451,11 @@ def ht_build_flags() -> int:
 
 def ht_wait_probe(ctx: int, cycles: int, stream=None) -> None:
     _check(_lib.ht_wait_probe(ctx, cycles, _stream(stream)))
+
+
+def ht_testing_set_wait_cycles(ctx: int, cycles: int) -> None:
+    """Testing: limit of the stream kernel's stage waits on this context (0: default)."""
+    _check(_lib.ht_testing_set_wait_cycles(ctx, cycles))
 
 
 def ht_check_probe(ctx: int, index: int, limit: int, stream=None) -> None:

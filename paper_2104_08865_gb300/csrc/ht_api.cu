@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "halftime.h"
+#include "halftime_testing.h"
 #include "ht_internal.h"
 #include "ht_check.cuh"
 #include "ht_runtime.h"
@@ -221,6 +222,19 @@ static int ensure_groups(ht_ctx *c, uint64_t groups_needed, cudaStream_t s) {
   return alloc_scratch(c, groups_needed + groups_needed / 4, strings);
 }
 
+// Zeroes the tree-group slots, the string sums and counts and the control
+// words (synchronous).
+static int reset_scratch(ht_ctx *c, cudaStream_t s) {
+  const size_t k = (size_t)c->ks->k;
+  HT_CUDA(cudaMemsetAsync(c->grp_acc, 0, c->cap_groups * k * 8 * sizeof(unsigned long long), s));
+  HT_CUDA(cudaMemsetAsync(c->grp_cnt, 0, c->cap_groups * sizeof(unsigned int), s));
+  HT_CUDA(cudaMemsetAsync(c->str_acc, 0, c->cap_strings * k * sizeof(unsigned long long), s));
+  HT_CUDA(cudaMemsetAsync(c->str_done, 0, c->cap_strings * sizeof(unsigned int), s));
+  HT_CUDA(cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), s));
+  HT_CUDA(cudaStreamSynchronize(s));
+  return HT_OK;
+}
+
 static Scratch scratch_view(const ht_ctx *c) {
   Scratch s;
   s.grp_acc = c->grp_acc;
@@ -247,6 +261,7 @@ void fill_keys(const ht_ctx *c, KParams &P) {
   }
   P.seeds = c->d_seeds;
   P.scr = scratch_view(c);
+  P.wait_cycles = c->wait_cycles;
 }
 
 // Dynamic shared memory of a stream-kernel block: per warp, `stages` slots of
@@ -285,15 +300,16 @@ static ht_shape default_shape() {
   return s;
 }
 
-// Strings below 32 MiB (length buckets up to 24) take 8-execution chunks
-// where the kernel set has them: one execution per thread instead of eight
-// in a row, eight times the warps.  Measured on GB300 (widths 24 and 40,
-// back-to-back launches): 64 KiB 8.2-12.3 us instead of 12.3-14.4, 1 MiB
-// 12.3-13.4 instead of 18.5-20.5, 16 MiB 16.4-17.0 instead of 22.0-22.6; at
-// 64 MiB 64-execution chunks are faster again.
+// Strings below 32 MiB (length buckets up to 24) take the block-chunk
+// kernel where the kernel set has it: one execution per thread instead of
+// eight in a row, and level 2 in shared memory.  Measured on GB300 (widths
+// 24 and 40, back-to-back launches): 1 MiB 8.3-10.3 us (8-execution warp
+// chunks 10.3-12.3, 64-execution warp chunks 16.4-17.9), 16 MiB 12.3-14.3
+// (14.5-16.4, 21.2-22.5); from 32 MiB on 64-execution warp chunks are
+// faster.
 static ht_shape default_shape(const KernelSet &ks, int bucket) {
   ht_shape s = default_shape();
-  if (bucket <= 24 && ks.single_aligned[0]) s.chunk_levels = 1;
+  if (bucket <= 24 && ks.block_single) s.kernel = 3;
   return s;
 }
 
@@ -307,6 +323,8 @@ static bool shape_ok(const KernelSet &ks, const ht_shape &s) {
   if (s.kernel == 0) return s.stages >= 2 && s.stages <= 8 && s.threads_per_block <= 256;
   if (s.kernel == 1)
     return s.chunk_levels >= 1 && s.chunk_levels <= 3 && s.threads_per_block <= 256;
+  // block-chunk kernel: eight warps per block, single strings only
+  if (s.kernel == 3) return ks.block_single != nullptr && s.threads_per_block == 256;
   return s.kernel == 2 && s.threads_per_block <= 256;
 }
 
@@ -314,14 +332,17 @@ static bool shape_ok(const KernelSet &ks, const ht_shape &s) {
 // plus the tail unit) or warp-chunk items (8^L executions each, two
 // 64-execution sub-chunks with 256-bit blocks; at least one).
 static uint64_t units_for(const KernelSet &ks, const ht_shape &s, uint64_t N) {
+  if (s.kernel == 3) return items_of(N, 2);  // block-chunk: 64-execution chunks
   return s.kernel != 1 ? ((N + 7) >> 3) + 1 : items_of(N, s.chunk_levels, ks.lanes);
 }
 static uint64_t unit_bytes(const KernelSet &ks, const ht_shape &s) {
+  if (s.kernel == 3) return (uint64_t)ks.exec_bytes << 6;
   if (s.kernel != 1) return (uint64_t)ks.exec_bytes << 3;
   return ((uint64_t)ks.exec_bytes * (uint64_t)(kLanes / ks.lanes)) << (3 * s.chunk_levels);
 }
 static uint64_t groups_for(const KernelSet &ks, const ht_shape &s, uint64_t N) {
   if (ks.tree) return bin_groups(N);
+  if (s.kernel == 3) return groups_of(N, 2);
   return groups_of(N, s.kernel != 1 ? 1 : s.chunk_levels);
 }
 
@@ -340,19 +361,30 @@ int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t 
     smem = stream_smem(ks, shape);
   } else if (shape.kernel == 2) {
     func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.range_single : ks.range_single_unaligned;
+  } else if (shape.kernel == 3) {
+    func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.block_single : ks.block_single_unaligned;
   } else {
     const int L = shape.chunk_levels;
     func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.single_aligned[L - 1] : ks.single_unaligned[L - 1];
   }
-  const int tpb = shape.threads_per_block;
+  int tpb = shape.threads_per_block;
   const int occ = occupancy(c, func, tpb, smem);
   if (occ == 0) return set_error(HT_ERR_ARG, "launch shape does not fit the device");
   const int bps = std::min(shape.blocks_per_sm, occ);
-  const uint64_t wpb = (uint64_t)tpb / 32;
-  // stream/range: a few units per warp at least; warp-chunk: one item per warp
-  const uint64_t per_warp = shape.kernel != 1 ? 4 : 1;
-  const uint64_t want = (u_end - u_begin + per_warp * wpb - 1) / (per_warp * wpb);
+  uint64_t wpb = (uint64_t)tpb / 32;
+  // stream/range: a few units per warp at least; warp-chunk: one item per
+  // warp; block-chunk: one item per block
+  const uint64_t per_warp = shape.kernel == 0 || shape.kernel == 2 ? 4 : 1;
+  const uint64_t want = shape.kernel == 3 ? u_end - u_begin
+                                          : (u_end - u_begin + per_warp * wpb - 1) / (per_warp * wpb);
   uint64_t grid = std::min<uint64_t>((uint64_t)c->num_sms * bps, want);
+  if (shape.kernel == 3) {
+    // whole rounds of blocks, as below for warps
+    const uint64_t items = u_end - u_begin;
+    const uint64_t bmax = (uint64_t)c->num_sms * bps;
+    const uint64_t rounds = (items + bmax - 1) / bmax;
+    grid = std::min(grid, (items + rounds - 1) / rounds);
+  }
   if (shape.kernel == 1) {
     // whole rounds: with R = ceil(items / max warps) rounds of cursor
     // grabs, ceil(items / R) warps finish together instead of a last round
@@ -362,6 +394,14 @@ int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t 
     const uint64_t rounds = (items + wmax - 1) / wmax;
     const uint64_t warps = (items + rounds - 1) / rounds;
     grid = std::min(grid, (warps + wpb - 1) / wpb);
+    if (rounds == 1 && grid < (uint64_t)c->num_sms) {
+      // one round on fewer blocks than SMs: smaller blocks spread it over
+      // every SM (on GB300, 64 MiB at width 24 took 25.2 us in 98 blocks of
+      // 8 warps and 18.6 us spread over all 152 SMs)
+      wpb = std::max<uint64_t>(1, warps / (uint64_t)c->num_sms);
+      tpb = (int)(32 * wpb);
+      grid = (warps + wpb - 1) / wpb;
+    }
   }
   grid = std::max<uint64_t>(grid, 1);
   KParams P;
@@ -374,7 +414,7 @@ int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t 
   P.total_warps = (unsigned)(grid * wpb);
   P.stages = (unsigned)shape.stages;
   void *args[] = {&P};
-  if (shape.kernel == 1 && (c->flags & HT_FLAG_OVERLAP_LAUNCHES)) {
+  if ((shape.kernel == 1 || shape.kernel == 3) && (c->flags & HT_FLAG_OVERLAP_LAUNCHES)) {
     // programmatic dependent launch: may start while the previous kernel of
     // the stream drains; the kernel waits before touching its scratch
     cudaLaunchConfig_t cfg = {};
@@ -423,6 +463,15 @@ static std::vector<ht_shape> tune_candidates(ht_ctx *c, bool batch) {
       h.threads_per_block = tpb;
       h.blocks_per_sm = bps;
       if (only_l2 || occupancy(c, batch ? ks.range_batch : ks.range_single, tpb, 0) < bps) continue;
+      cands.push_back(h);
+    }
+  if (!batch && ks.block_single)
+    for (int bps : {1, 2, 3, 4, 6, 8}) {
+      ht_shape h = default_shape();
+      h.kernel = 3;
+      h.threads_per_block = 256;
+      h.blocks_per_sm = bps;
+      if (occupancy(c, ks.block_single, 256, 0) < bps) continue;
       cands.push_back(h);
     }
   for (int L : {1, 2, 3})
@@ -558,7 +607,24 @@ int ht_ctx_reserve(ht_ctx *c, uint64_t max_total_bytes, size_t max_strings) {
 
 int ht_ctx_status(ht_ctx *c, ht_stream_t stream) {
   if (!c) return set_error(HT_ERR_ARG, "ht_ctx_status: NULL context");
-  return read_status(c->ctl, (cudaStream_t)stream);
+  const int rc = read_status(c->ctl, (cudaStream_t)stream);
+  if (rc == HT_ERR_DEVICE) {
+    // a kernel that gave up (a wait that ran out, an access the checked build
+    // skipped) can leave tree groups, string sums and the cursor half
+    // written: clear the scratch so that the next call starts clean
+    char msg[256];
+    ht_last_error(msg, sizeof msg);
+    const int rr = reset_scratch(c, (cudaStream_t)stream);
+    if (rr) return rr;
+    return set_error(rc, "%s", msg);
+  }
+  return rc;
+}
+
+int ht_testing_set_wait_cycles(ht_ctx *c, uint64_t cycles) {
+  if (!c || cycles > (1ull << 34)) return set_error(HT_ERR_ARG, "ht_testing_set_wait_cycles: bad arguments");
+  c->wait_cycles = (long long)cycles;
+  return HT_OK;
 }
 
 int ht_hash(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest, ht_stream_t stream) {
@@ -591,7 +657,7 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
   // pieces of whole units, about 64 MiB each (whole 64-execution chunks for
   // the unit-based kernels); a slot also holds the tail
   uint64_t units_per_piece = std::max<uint64_t>(1, (64ull << 20) / ub);
-  if (shape.kernel != 1) units_per_piece = std::max<uint64_t>(8, units_per_piece & ~7ull);
+  if (shape.kernel == 0 || shape.kernel == 2) units_per_piece = std::max<uint64_t>(8, units_per_piece & ~7ull);
   const uint64_t slot_bytes = ((units_per_piece * ub + B + 255) / 256) * 256;
   if (!c->copy_stream) HT_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
   if (c->stage_bytes < slot_bytes) {
@@ -848,7 +914,8 @@ int ht_get_shape(ht_ctx *c, uint64_t len, ht_shape *out) {
 }
 
 int ht_set_shape(ht_ctx *c, uint64_t len, const ht_shape *shape) {
-  if (!c || !shape || !shape_ok(*c->ks, *shape)) return set_error(HT_ERR_ARG, "ht_set_shape: bad shape");
+  if (!c || !shape || !shape_ok(*c->ks, *shape) || (len == UINT64_MAX && shape->kernel == 3))
+    return set_error(HT_ERR_ARG, "ht_set_shape: bad shape");
   c->shapes[bucket_of(len)] = *shape;
   return HT_OK;
 }
@@ -878,25 +945,32 @@ int ht_autotune(ht_ctx *c, uint64_t len, ht_stream_t stream, ht_shape *best) {
   if (!c || len == UINT64_MAX) return set_error(HT_ERR_ARG, "ht_autotune: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   const std::vector<ht_shape> cands = tune_candidates(c, false);
+  // strings shorter than the L2 cache would be timed from L2: successive
+  // launches take successive copies in a buffer of at least 384 MiB, so
+  // that every launch reads its bytes from HBM, as a fresh request does
+  const uint64_t stride = (std::max<uint64_t>(len, 16) + 255) & ~255ull;
+  const uint64_t copies = std::max<uint64_t>(1, (384ull << 20) / stride);
+  const uint64_t span = stride * copies;
   uint8_t *buf = nullptr;
-  HT_CUDA(cudaMalloc((void **)&buf, std::max<uint64_t>(len, 16)));
+  HT_CUDA(cudaMalloc((void **)&buf, span));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int rc = HT_OK;
-  cudaError_t ce = cudaMemsetAsync(buf, 0x5A, std::max<uint64_t>(len, 16), s);
+  cudaError_t ce = cudaMemsetAsync(buf, 0x5A, span, s);
   if (ce != cudaSuccess) rc = cuda_error(ce, "cudaMemsetAsync");
   const int bk = bucket_of(len);
   const ht_shape saved = c->shapes[bk];
   ht_shape winner = saved;
   float best_ms = 1e30f;
+  uint64_t turn = 0;
   for (size_t i = 0; i < cands.size() && rc == HT_OK; ++i) {
     c->shapes[bk] = cands[i];
-    rc = ht_hash(c, buf, len, c->d_digest, stream);  // warm-up
+    rc = ht_hash(c, buf + (turn++ % copies) * stride, len, c->d_digest, stream);  // warm-up
     float times[3] = {0, 0, 0};
     for (int r = 0; r < 3 && rc == HT_OK; ++r) {
       cudaEventRecord(e0, s);
-      rc = ht_hash(c, buf, len, c->d_digest, stream);
+      rc = ht_hash(c, buf + (turn++ % copies) * stride, len, c->d_digest, stream);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       cudaEventElapsedTime(&times[r], e0, e1);

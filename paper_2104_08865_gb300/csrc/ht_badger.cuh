@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(256, 2) bin_kernel(const __grid_constant__ KPa
         item = P.item_begin + gw;
         first = false;
       } else {
+        if (P.item_end - P.item_begin <= P.total_warps) break;
         if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
         item = __shfl_sync(kFull, item, 0) + P.item_begin + P.total_warps;
       }

@@ -118,21 +118,36 @@ int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, c
   sp.chunk0 = C;
   sp.n_items = 0xffffffffu;
   void *args[] = {&P};
-  const void *func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.inc_aligned : ks.inc_unaligned;
-  int bps = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, func, kTpb, 0);
-  if (e != cudaSuccess) return cuda_error(e, "occupancy");
-  bps = std::max(1, std::min(bps, 2));
-  const uint64_t wpb = kTpb / 32;
-  // whole rounds of cursor grabs (see the one-shot launch)
-  const uint64_t wmax = (uint64_t)c->num_sms * bps * wpb;
-  const uint64_t rounds = (M + wmax - 1) / wmax;
-  const uint64_t warps = (M + rounds - 1) / rounds;
-  const uint64_t grid = std::max<uint64_t>(1, (warps + wpb - 1) / wpb);
+  const bool aligned = (((uintptr_t)sp.ptr) & 15u) == 0;
+  // updates below 32 MiB: the block-chunk kernel (a block of eight warps
+  // per chunk, one execution per thread), as for one-shot strings
+  const bool blockwise = M * h->granule < (32ull << 20);
+  const void *func = blockwise ? (aligned ? ks.inc_block_aligned : ks.inc_block_unaligned)
+                               : (aligned ? ks.inc_aligned : ks.inc_unaligned);
+  const int bps = 2;  // (both kernels fit two blocks of 256 threads per SM)
+  uint64_t wpb = kTpb / 32, grid;
+  if (blockwise) {
+    // one chunk per block, whole rounds of blocks
+    const uint64_t bmax = (uint64_t)c->num_sms * bps;
+    const uint64_t rounds = (M + bmax - 1) / bmax;
+    grid = (M + rounds - 1) / rounds;
+  } else {
+    // whole rounds of cursor grabs (see the one-shot launch), one round
+    // spread over every SM
+    const uint64_t wmax = (uint64_t)c->num_sms * bps * wpb;
+    const uint64_t rounds = (M + wmax - 1) / wmax;
+    const uint64_t warps = (M + rounds - 1) / rounds;
+    grid = std::max<uint64_t>(1, (warps + wpb - 1) / wpb);
+    if (rounds == 1 && grid < (uint64_t)c->num_sms) {
+      wpb = std::max<uint64_t>(1, warps / (uint64_t)c->num_sms);
+      grid = (warps + wpb - 1) / wpb;
+    }
+  }
+  grid = std::max<uint64_t>(grid, 1);
   P.item_begin = C;
   P.item_end = C + M;
   P.total_warps = (unsigned)(grid * wpb);
-  e = cudaLaunchKernel(func, dim3((unsigned)grid), dim3(kTpb), args, 0, s);
+  cudaError_t e = cudaLaunchKernel(func, dim3((unsigned)grid), dim3((unsigned)(32 * wpb)), args, 0, s);
   if (e != cudaSuccess) return cuda_error(e, "incremental update launch");
   c->launches.fetch_add(1);
   h->chunks = C + M;

@@ -78,6 +78,7 @@ struct KParams {
   unsigned int count;           // batch mode: strings
   unsigned int total_warps;     // warps in the grid
   unsigned int stages;          // stream kernel: shared-memory slots per warp
+  long long wait_cycles;        // stream kernel: limit of a stage wait (0: the default, about 1 s)
 };
 
 struct PlanArgs {
@@ -121,6 +122,8 @@ struct KernelSet {
   const void *plan_items;           //   the string of every work item
   const void *stream_single;
   const void *stream_batch;
+  const void *block_single;  // block-chunk kernel: a block of 8 warps per 64-execution chunk
+  const void *block_single_unaligned;
   const void *range_single;  // hybrid kernel: chunks then units from a cursor
   const void *range_single_unaligned;
   const void *range_batch;   // [aligned-only, general] pair, see ctl.unaligned
@@ -129,6 +132,8 @@ struct KernelSet {
   const void *part_finish;  // parts: climb merged groups, write the digest
   const void *inc_aligned;    // incremental: whole chunks of one update
   const void *inc_unaligned;
+  const void *inc_block_aligned;    // the same with the block-chunk kernel (short updates)
+  const void *inc_block_unaligned;
   const void *inc_stack;      // incremental: pending stack nodes into the sum
   const void *wait_probe;     // a bounded wait that runs out (tests the timeout path)
   int exec_bytes, k, n_seed, off_T, off_F, off_R, ew;

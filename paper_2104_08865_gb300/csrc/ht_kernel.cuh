@@ -808,6 +808,8 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
       item = P.item_begin + gw;
       first = false;
     } else {
+      // a launch of one round hands nothing out through the cursor
+      if (P.item_end - P.item_begin <= P.total_warps) break;
       if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
       item = __shfl_sync(kFull, item, 0) + P.item_begin + P.total_warps;
     }

@@ -32,6 +32,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 constexpr size_t kOffCtl = 0;
 constexpr size_t kOffSeeds = 256;
 constexpr size_t kSeedBytes = 57344;  // >= 6897 seed words (width 40)
+static_assert(kSeedBytes >= ht::Dims<40>::n_seed * sizeof(uint64_t) &&
+                  kSeedBytes >= ht::Dims<32>::n_seed * sizeof(uint64_t),
+              "the seed region holds the largest seed layout");
 constexpr size_t kOffStrAcc = kOffSeeds + kSeedBytes;
 constexpr size_t kOffStrDone = kOffStrAcc + 256;
 constexpr size_t kOffGroups = kOffStrDone + 256;
@@ -44,6 +47,9 @@ int g_sms[kMaxDevices] = {};
 
 // Device address of the array on the current device, looked up once per
 // device (host code only holds a stand-in for the symbol, not its address).
+// The same first call loads every kernel this entry point may launch, for
+// every width: with lazy module loading a kernel's module is otherwise
+// loaded, with driver-side allocations, at its first launch.
 int scratch_on_current_device(unsigned char **addr, int *sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -57,6 +63,14 @@ int scratch_on_current_device(unsigned char **addr, int *sms) {
     int n = 0;
     e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return ht::cuda_error(e, "cudaDeviceGetAttribute");
+    for (int w : {16, 24, 32, 40}) {
+      const ht::KernelSet *ks = ht::kernel_set(w);
+      for (const void *f : {ks->single_aligned[kChunkLevels - 1], ks->single_unaligned[kChunkLevels - 1]}) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return ht::cuda_error(e, "cudaFuncGetAttributes(no-alloc kernels)");
+      }
+    }
     g_addr[dev] = static_cast<unsigned char *>(p);
     g_sms[dev] = n;
   }
@@ -80,7 +94,8 @@ extern "C" int ht_hash_noalloc(int width_bytes, const uint64_t *seed_words_host,
                                ht_stream_t stream) {
   const ht::KernelSet *ks = ht::kernel_set(width_bytes);
   if (!ks || ks->lanes != ht::kLanes || ks->tree) return ht::set_error(HT_ERR_WIDTH, "unsupported width %d", width_bytes);
-  if (!seed_words_host || n_words != (size_t)ks->n_seed || !digest_dev || (len && !data_dev))
+  if (!seed_words_host || n_words != (size_t)ks->n_seed || !digest_dev || (len && !data_dev) ||
+      n_words * sizeof(uint64_t) > kSeedBytes)
     return ht::set_error(HT_ERR_ARG, "ht_hash_noalloc: bad arguments (need %d seed words)", ks->n_seed);
   const uint64_t N = len / (uint64_t)ks->exec_bytes;
   const uint64_t groups = ht::groups_of(N, kChunkLevels);

@@ -14,6 +14,7 @@
 // as in the stream kernel.
 #pragma once
 
+#include "ht_block.cuh"
 #include "ht_inc.cuh"
 #include "ht_parts.cuh"
 #include "ht_stream.cuh"
@@ -273,6 +274,8 @@ KernelSet make_kernel_set() {
   ks.plan_write[3] = (const void *)plan_write_kernel<W, 3>;
   ks.stream_single = (const void *)stream_kernel<W, false>;
   ks.stream_batch = (const void *)stream_kernel<W, true>;
+  ks.block_single = (const void *)block_kernel<W, true>;
+  ks.block_single_unaligned = (const void *)block_kernel<W, false>;
   ks.range_single = (const void *)range_kernel<W, false, true>;
   ks.range_single_unaligned = (const void *)range_kernel<W, false, false>;
   ks.range_batch = (const void *)range_kernel<W, true, true>;
@@ -281,6 +284,8 @@ KernelSet make_kernel_set() {
   ks.part_finish = (const void *)part_finish_kernel<W, 2>;
   ks.inc_aligned = (const void *)hash_kernel<W, 2, true, true, true>;
   ks.inc_unaligned = (const void *)hash_kernel<W, 2, true, false, true>;
+  ks.inc_block_aligned = (const void *)block_kernel<W, true, true>;
+  ks.inc_block_unaligned = (const void *)block_kernel<W, false, true>;
   ks.inc_stack = (const void *)inc_stack_kernel<W>;
   ks.wait_probe = (const void *)wait_probe_kernel<W>;
   ks.exec_bytes = Dims<W>::exec_bytes;

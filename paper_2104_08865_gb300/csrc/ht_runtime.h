@@ -63,6 +63,7 @@ struct ht_ctx {
   bool part_open = false;
   bool part_owned = false;  // part_buf allocated by the library
   std::atomic<uint64_t> launches{0};
+  long long wait_cycles = 0;  // testing: limit of the stream kernel's stage waits (0: default)
   // blocks per SM of (kernel, threads per block, dynamic shared memory),
   // queried once per context (the query costs more than a small launch)
   struct Occ {

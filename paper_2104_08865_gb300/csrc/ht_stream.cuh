@@ -325,7 +325,8 @@ __global__ void __launch_bounds__(256) stream_kernel(const __grid_constant__ KPa
       uint64_t y[2][k];
       if (aligned16(sp.ptr)) {
         const unsigned sl = (unsigned)(cseq % R);
-        if (!mbar_wait(bars + 8 * sl, (uint32_t)((cseq / R) & 1))) failed = true;
+        if (!mbar_wait(bars + 8 * sl, (uint32_t)((cseq / R) & 1), P.wait_cycles > 0 ? P.wait_cycles : kWaitCycles))
+          failed = true;
         failed = __any_sync(kFull, failed);
         if (failed) break;
         const uint32_t base = slots + sl * SLOT + x * B + p * 16;
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(256) stream_kernel(const __grid_constant__ KPa
   if (failed) {
     if (ln == 0) atomicOr(&P.scr.ctl->status, kStatusTimeout);
     // let the copies already issued land before the block's shared memory
-    // is released (bounded as well)
+    // is released (bounded as well, with the default limit)
     if (ln == 0)
       for (uint64_t sq = cseq; sq < pseq; ++sq) mbar_wait(bars + 8 * (unsigned)(sq % R), (uint32_t)((sq / R) & 1));
     __syncwarp();

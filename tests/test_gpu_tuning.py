@@ -30,20 +30,32 @@ def _u64(t):
 
 
 def test_default_shapes_by_length(dev):
-    """Strings below 32 MiB default to 8-execution chunks, longer ones and
-    batches to 64-execution chunks; the 256-bit-block variant and the
-    binary-tree ablation keep 64-execution items everywhere."""
+    """Strings below 32 MiB default to the block-chunk kernel, longer ones and
+    batches to 64-execution warp chunks; the 256-bit-block variant and the
+    binary-tree ablation keep 64-execution warp items everywhere; the
+    block-chunk kernel is refused for batches."""
     from paper_2104_08865_gb300 import abi
-    h, _ = _pair(24)
+    h, ref = _pair(24)
     for n in (0, 1, 1000, 1 << 20, (32 << 20) - 1):
-        assert abi.ht_get_shape(h.ctx, n)["chunk_levels"] == 1, n
+        assert abi.ht_get_shape(h.ctx, n)["kernel"] == 3, n
     for n in (32 << 20, 1 << 30, 2**64 - 1):
-        assert abi.ht_get_shape(h.ctx, n)["chunk_levels"] == 2, n
+        s = abi.ht_get_shape(h.ctx, n)
+        assert s["kernel"] == 1 and s["chunk_levels"] == 2, n
+    with pytest.raises(abi.HalftimeError) as e:
+        abi.ht_set_shape(h.ctx, 2**64 - 1, kernel=3, chunk_levels=2, threads_per_block=256, blocks_per_sm=2)
+    assert e.value.code == abi.HT_ERR_ARG
+    # the defaults on either side of the boundary, and mid-size strings whose
+    # one round is spread over every SM with smaller blocks
+    dbuf = inputs.stream_bytes_torch(4, 0, (80 << 20) + 300, dev)
+    host = dbuf.cpu().numpy()
+    for n in ((32 << 20) - 1, 32 << 20, (40 << 20) + 77, (80 << 20) + 300):
+        assert np.array_equal(_u64(h.hash(dbuf, n)), oracle.hash_bytes(24, ref, host[:n])), n
     h.close()
     for code in (24 | abi.HT_BLOCK_256, 24 | abi.HT_TREE_BINARY):
         h, _ = _pair(24, code)
         for n in (1000, 1 << 20, 1 << 30, 2**64 - 1):
-            assert abi.ht_get_shape(h.ctx, n)["chunk_levels"] == 2
+            s = abi.ht_get_shape(h.ctx, n)
+            assert s["kernel"] == 1 and s["chunk_levels"] == 2
         h.close()
 
 
@@ -86,7 +98,8 @@ def test_autotune_batch_50000_log_uniform(dev):
     h.close()
 
 
-@pytest.mark.parametrize("shape", [dict(kernel=1, chunk_levels=1, threads_per_block=128, blocks_per_sm=4),
+@pytest.mark.parametrize("shape", [dict(kernel=1, chunk_levels=2, threads_per_block=256, blocks_per_sm=2),
+                                   dict(kernel=1, chunk_levels=1, threads_per_block=128, blocks_per_sm=4),
                                    dict(kernel=1, chunk_levels=3, threads_per_block=256, blocks_per_sm=2),
                                    dict(kernel=0, chunk_levels=2, stages=3, threads_per_block=128, blocks_per_sm=2),
                                    dict(kernel=2, chunk_levels=2, threads_per_block=256, blocks_per_sm=2)])

@@ -638,3 +638,36 @@ def test_b4_python_evaluation(width):
             want.append(acc)
         got = oracle.hash_bytes(width, seeds, data, b=b)
         assert [int(v) for v in got] == want, (width, N)
+
+
+# ------------------------------------------------- collision rate of a window
+
+@pytest.mark.parametrize("v,half", [(10, "lo"), (12, "hi"), (16, "lo")])
+def test_tail_window_collision_rate(v, half):
+    """Two strings that differ only in one tail word w -> w' = w ^ 2^v (in its
+    low or high 32-bit half) differ in output word t by the difference of one
+    NH term, (A)(B) - (A')(B') with one factor equal in both; the other
+    factor is uniform when the data are.  Their low 16 bits then collide
+    with probability exactly 2^(v-16) (v <= 16).  Count the collisions of
+    out_0 over random tail-only strings under one seed and compare with that
+    rate (a mistake that drops, repeats or misroutes the tail word moves the
+    count far outside the band)."""
+    width = 24
+    xb = oracle.params(width)["exec_bytes"]
+    seeds = _seeds(width, 71)
+    rng = np.random.default_rng(v * 7 + (half == "hi"))
+    trials = 6000 if v >= 12 else 20000
+    hits = 0
+    for _ in range(trials):
+        n = int(rng.integers(8, xb))  # tail only: no whole execution
+        data = rng.integers(0, 256, n, dtype=np.uint8)
+        m = int(rng.integers(0, n // 8))  # a whole tail word
+        other = data.copy()
+        bit = v + (32 if half == "hi" else 0)
+        other[8 * m + bit // 8] ^= np.uint8(1 << (bit % 8))
+        a = int(oracle.hash_bytes(width, seeds, data)[0])
+        b = int(oracle.hash_bytes(width, seeds, other)[0])
+        hits += (a & 0xFFFF) == (b & 0xFFFF)
+    p = 2.0 ** (min(v, 16) - 16)
+    mean, sd = trials * p, math.sqrt(trials * p * (1 - p))
+    assert abs(hits - mean) <= 6 * sd + 1, (hits, mean, sd)

@@ -4,13 +4,14 @@ It exists for callers that cannot allocate device memory (inside another
 framework's allocator hooks, under another framework's memory pool, or on a
 path that cannot take cudaMalloc's synchronisation): it keeps its scratch in a
 fixed array the library reserves at load time.  These tests call it through
-the C ABI and require the same digests as ht_hash (bit for bit: the hash is
-integer arithmetic) on consecutive calls, which share and re-clear that array.
-The file is named so that pytest collects it last.
+the C ABI and require the same digests as ht_hash and as the CPU oracle (bit
+for bit: the hash is integer arithmetic) on consecutive calls, which share
+and re-clear that array.  The file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2104_08865_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -37,6 +38,8 @@ def test_noalloc_matches_ht_hash_on_consecutive_calls(dev, width):
     long_n = (5 * 512 + 3 * 64 + 2) * 8 * xb + 77
     lens = [long_n, long_n, 9 * 64 * xb + 5, 0]
     data = inputs.stream_bytes_torch(8, 0, long_n + 16, dev)
+    host = data.cpu().numpy()
+    ref_seeds = oracle.seed_expand(7, oracle.seed_words(width))
     stream = torch.cuda.current_stream()
     for n in lens:
         want = h.hash(data, n)
@@ -44,6 +47,8 @@ def test_noalloc_matches_ht_hash_on_consecutive_calls(dev, width):
         abi.ht_hash_noalloc(width, seeds, data.data_ptr(), n, got.data_ptr(), stream)
         torch.cuda.synchronize()
         assert torch.equal(got, want), (width, n)
+        assert np.array_equal(got.cpu().numpy().view(np.uint64),
+                              oracle.hash_bytes(width, ref_seeds, host[:n])), (width, n)
     # a string that does not start on a 16-byte boundary
     n = 70 * xb + 100
     want = h.hash(data, n, offset=3)
@@ -51,6 +56,7 @@ def test_noalloc_matches_ht_hash_on_consecutive_calls(dev, width):
     abi.ht_hash_noalloc(width, seeds, data.data_ptr() + 3, n, got.data_ptr(), stream)
     torch.cuda.synchronize()
     assert torch.equal(got, want)
+    assert np.array_equal(got.cpu().numpy().view(np.uint64), oracle.hash_bytes(width, ref_seeds, host[3:3 + n]))
     h.close()
 
 
