@@ -610,14 +610,29 @@ def run_size_sweep_leg(args, dev, stream, data):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 lone.append(e0.elapsed_time(e1) * 1000)
+            # the same back to back with HT_FLAG_OVERLAP_LAUNCHES (each launch
+            # may start while the one before it drains)
+            abi.ht_ctx_set_flags(h.ctx, abi.HT_FLAG_OVERLAP_LAUNCHES)
+            for i in range(3):
+                abi.ht_hash(h.ctx, at[i], n, out.data_ptr(), stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for i in range(reps):
+                abi.ht_hash(h.ctx, at[i], n, out.data_ptr(), stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            us_ov = e0.elapsed_time(e1) * 1000 / reps
+            abi.ht_ctx_set_flags(h.ctx, 0)
             shape = abi.ht_get_shape(h.ctx, n)
             rows.append({"width": w, "mib": mib, "us": round(us, 2), "gbs": round(n / us / 1e3, 1),
+                         "overlapped_us": round(us_ov, 2), "overlapped_gbs": round(n / us_ov / 1e3, 1),
                          "lone_us": round(statistics.median(lone), 2),
                          "kernel": {1: "warp-chunk", 3: "block-chunk"}.get(shape["kernel"], shape["kernel"]),
                          "chunk_levels": shape["chunk_levels"]})
         h.status()
         h.close()
-    return {"note": "per-launch time, default shape per length; us = back-to-back mean, "
+    return {"note": "per-launch time, default shape per length, cold pieces; us = back-to-back mean, "
+                    "overlapped_us = the same with HT_FLAG_OVERLAP_LAUNCHES, "
                     "lone_us = median of one launch between events", "rows": rows}
 
 
@@ -639,7 +654,7 @@ def run_serving(args, dev, stream):
     h = Hasher(32, seed_words=abi.ht_seed_expand(SEED_KEY, 32))
     mean_len = None
     out = {"workload": "width 32, lengths log-uniform 256 B..64 MiB, Poisson arrivals, budget 16 GiB, "
-                       "%.1f s per load point" % args.serve_seconds, "forms": {},
+                       "8 batches in flight, %.1f s per load point" % args.serve_seconds, "forms": {},
            "form_notes": {"device": "requests already in device memory",
                           "pinned_h2d": "pinned host requests read in place by the batch kernel over "
                                         "the CPU-GPU link (the server's default)",
@@ -660,7 +675,7 @@ def run_serving(args, dev, stream):
         # milliseconds of work; the better of two
         nburst = 10000 if form == "device" else 2000
         ln, off = requests(nburst, 61)
-        srv = abi.ht_server_create(h.ctx, 16 << 30, n_streams=4, max_batch=4096, pinned_mode=mode)
+        srv = abi.ht_server_create(h.ctx, 16 << 30, n_streams=8, max_batch=4096, pinned_mode=mode)
         dig = np.zeros((nburst, 4), dtype=np.uint64)
         peak = 0.0
         for _ in range(2):
@@ -676,16 +691,31 @@ def run_serving(args, dev, stream):
         for frac in args.serve_loads:
             rate = frac * peak * 1e9 / mean_len  # requests per second
             n = max(50, int(rate * args.serve_seconds))
-            ln, off = requests(n, 63)
-            gaps = rng.exponential(1e6 / rate, n)
-            arr = np.cumsum(gaps) - gaps[0]
-            dig = np.zeros((n, 4), dtype=np.uint64)
-            late = abi.ht_server_replay(srv, base + off, ln, [pinned] * n, arr, dig)
-            st = abi.ht_server_stats(srv, reset=True)
-            res["points"].append({"load": frac, "offered_gbs": round(frac * peak, 1),
-                                  "requests": n, "achieved_gbs": round(st["bytes_completed"] / st["wall_s"] / 1e9, 1),
-                                  "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
-                                  "max_submit_delay_us": round(late, 1), "batches": int(st["batches"])})
+            # device-resident requests below saturation: several runs of the
+            # point (fresh arrivals each), the median run reported with the
+            # spread of p50 and p99
+            runs = args.serve_repeats if (form == "device" and frac < 1) else 1
+            sts = []
+            for _ in range(runs):
+                ln, off = requests(n, 63)
+                gaps = rng.exponential(1e6 / rate, n)
+                arr = np.cumsum(gaps) - gaps[0]
+                dig = np.zeros((n, 4), dtype=np.uint64)
+                late = abi.ht_server_replay(srv, base + off, ln, [pinned] * n, arr, dig)
+                st = abi.ht_server_stats(srv, reset=True)
+                st["late"] = late
+                sts.append(st)
+            sts.sort(key=lambda v: v["p99_us"])
+            st = sts[len(sts) // 2]
+            pt = {"load": frac, "offered_gbs": round(frac * peak, 1),
+                  "requests": n, "achieved_gbs": round(st["bytes_completed"] / st["wall_s"] / 1e9, 1),
+                  "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
+                  "max_submit_delay_us": round(st["late"], 1), "batches": int(st["batches"])}
+            if runs > 1:
+                pt["runs"] = runs
+                pt["p50_us_range"] = [round(min(v["p50_us"] for v in sts), 1), round(max(v["p50_us"] for v in sts), 1)]
+                pt["p99_us_range"] = [round(sts[0]["p99_us"], 1), round(sts[-1]["p99_us"], 1)]
+            res["points"].append(pt)
         abi.ht_server_destroy(srv)
         out["forms"][form] = res
     out["mean_len_bytes"] = round(mean_len)
@@ -903,6 +933,8 @@ def main():
     ap.add_argument("--batch-strings", type=int, default=50_000)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-repeats", type=int, default=3,
+                    help="runs of each device-form load point below saturation")
     ap.add_argument("--serve-pool", type=int, default=2 * GIB)
     ap.add_argument("--serve-loads", type=lambda v: [float(x) for x in v.split(",")],
                     default=[0.1, 0.5, 0.9, 1.2])

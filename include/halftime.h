@@ -472,12 +472,15 @@ int ht_hash_noalloc(int width_bytes, const uint64_t *seed_words_host,
  *     executions from an atomic cursor and load them with 128-bit loads;
  *   kernel 2, the hybrid kernel: like kernel 1 with 64-execution chunks, but
  *     the last stretch of the launch is handed out as single 8-execution
- *     units.
+ *     units;
+ *   kernel 3, the block-chunk kernel (single strings only; the default below
+ *     32 MiB): a block of eight warps takes a 64-execution chunk, one
+ *     execution per thread, level 2 in shared memory; threads_per_block 256.
  * A shape also fixes the threads per block and blocks per SM.  The context
  * caches one shape per length bucket (bucket = floor(log2(len)), 0..63) and
  * one for batches. */
 typedef struct ht_shape {
-  int kernel;            /* 0: stream, 1: warp-chunk, 2: hybrid kernel */
+  int kernel;            /* 0: stream, 1: warp-chunk, 2: hybrid, 3: block-chunk */
   int chunk_levels;      /* warp-chunk kernel: L = 1, 2 or 3 */
   int stages;            /* stream kernel: shared-memory stages per warp, 2..8 */
   int threads_per_block; /* multiple of 32, at most 256 */
@@ -529,7 +532,7 @@ uint64_t ht_ctx_launches(ht_ctx *ctx);
  * request's arrival, launch and completion times are recorded (host
  * steady clock) for latency percentiles. */
 typedef struct ht_server_opts {
-  int n_streams;          /* concurrent batches in flight (default 4) */
+  int n_streams;          /* concurrent batches in flight (default 8) */
   size_t max_batch;       /* requests per batch (default 4096) */
   size_t max_queue;       /* queued requests before submit says BUSY (default 1<<20) */
   uint64_t max_wait_us;   /* longest a request waits for batch-mates (default 0) */

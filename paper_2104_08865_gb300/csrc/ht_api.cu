@@ -348,75 +348,57 @@ static uint64_t groups_for(const KernelSet &ks, const ht_shape &s, uint64_t N) {
 
 // ---- single-string launch -------------------------------------------------------
 
-// Launches one kernel over units [u_begin, u_end) of the string described by
-// sp (sp.n_items = all units of the string).  digest_dev receives k words
-// when the string's last unit completes.
-int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t u_begin,
-                  uint64_t u_end, uint64_t *digest_dev, cudaStream_t s) {
-  const KernelSet &ks = *c->ks;
-  const void *func;
-  size_t smem = 0;
-  if (shape.kernel == 0) {
-    func = ks.stream_single;
-    smem = stream_smem(ks, shape);
-  } else if (shape.kernel == 2) {
-    func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.range_single : ks.range_single_unaligned;
-  } else if (shape.kernel == 3) {
-    func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.block_single : ks.block_single_unaligned;
-  } else {
-    const int L = shape.chunk_levels;
-    func = (((uintptr_t)sp.ptr) & 15u) == 0 ? ks.single_aligned[L - 1] : ks.single_unaligned[L - 1];
+// The kernel of a shape for a string.
+static const void *single_func(const KernelSet &ks, const ht_shape &shape, const StrPlan &sp) {
+  const bool al = (((uintptr_t)sp.ptr) & 15u) == 0;
+  switch (shape.kernel) {
+    case 0: return ks.stream_single;
+    case 2: return al ? ks.range_single : ks.range_single_unaligned;
+    case 3: return al ? ks.block_single : ks.block_single_unaligned;
+    default: return al ? ks.single_aligned[shape.chunk_levels - 1] : ks.single_unaligned[shape.chunk_levels - 1];
   }
-  int tpb = shape.threads_per_block;
-  const int occ = occupancy(c, func, tpb, smem);
-  if (occ == 0) return set_error(HT_ERR_ARG, "launch shape does not fit the device");
-  const int bps = std::min(shape.blocks_per_sm, occ);
-  uint64_t wpb = (uint64_t)tpb / 32;
-  // stream/range: a few units per warp at least; warp-chunk: one item per
-  // warp; block-chunk: one item per block
-  const uint64_t per_warp = shape.kernel == 0 || shape.kernel == 2 ? 4 : 1;
-  const uint64_t want = shape.kernel == 3 ? u_end - u_begin
-                                          : (u_end - u_begin + per_warp * wpb - 1) / (per_warp * wpb);
+}
+
+// Grid of one launch over `items` work items: blocks of *tpb threads (the
+// block-chunk kernel: one item per block; the warp-chunk kernel: one item
+// per warp, in whole rounds, a single round spread over every SM; stream
+// and hybrid kernels: a few units per warp).
+static uint64_t grid_for(const ht_ctx *c, int kernel, uint64_t items, int bps, int *tpb) {
+  uint64_t wpb = (uint64_t)*tpb / 32;
+  const uint64_t per_warp = kernel == 0 || kernel == 2 ? 4 : 1;
+  const uint64_t want = kernel == 3 ? items : (items + per_warp * wpb - 1) / (per_warp * wpb);
   uint64_t grid = std::min<uint64_t>((uint64_t)c->num_sms * bps, want);
-  if (shape.kernel == 3) {
+  if (kernel == 3) {
     // whole rounds of blocks, as below for warps
-    const uint64_t items = u_end - u_begin;
     const uint64_t bmax = (uint64_t)c->num_sms * bps;
     const uint64_t rounds = (items + bmax - 1) / bmax;
     grid = std::min(grid, (items + rounds - 1) / rounds);
   }
-  if (shape.kernel == 1) {
+  if (kernel == 1) {
     // whole rounds: with R = ceil(items / max warps) rounds of cursor
     // grabs, ceil(items / R) warps finish together instead of a last round
     // that only a few warps work on
-    const uint64_t items = u_end - u_begin;
     const uint64_t wmax = (uint64_t)c->num_sms * bps * wpb;
     const uint64_t rounds = (items + wmax - 1) / wmax;
     const uint64_t warps = (items + rounds - 1) / rounds;
     grid = std::min(grid, (warps + wpb - 1) / wpb);
     if (rounds == 1 && grid < (uint64_t)c->num_sms) {
       // one round on fewer blocks than SMs: smaller blocks spread it over
-      // every SM (on GB300, 64 MiB at width 24 took 25.2 us in 98 blocks of
-      // 8 warps and 18.6 us spread over all 152 SMs)
+      // every SM
       wpb = std::max<uint64_t>(1, warps / (uint64_t)c->num_sms);
-      tpb = (int)(32 * wpb);
+      *tpb = (int)(32 * wpb);
       grid = (warps + wpb - 1) / wpb;
     }
   }
-  grid = std::max<uint64_t>(grid, 1);
-  KParams P;
-  fill_keys(c, P);
-  P.single = sp;
-  P.item_begin = u_begin;
-  P.item_end = u_end;
-  P.digests = (unsigned long long *)digest_dev;
-  P.count = 1;
-  P.total_warps = (unsigned)(grid * wpb);
-  P.stages = (unsigned)shape.stages;
+  return std::max<uint64_t>(grid, 1);
+}
+
+static int launch_kernel(const void *func, uint64_t grid, int tpb, size_t smem, KParams &P, bool pdl,
+                         cudaStream_t s) {
   void *args[] = {&P};
-  if ((shape.kernel == 1 || shape.kernel == 3) && (c->flags & HT_FLAG_OVERLAP_LAUNCHES)) {
-    // programmatic dependent launch: may start while the previous kernel of
-    // the stream drains; the kernel waits before touching its scratch
+  if (pdl) {
+    // programmatic dependent launch: may start while the kernel before it in
+    // the stream is still running (the kernel waits where that matters)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(tpb);
@@ -431,6 +413,34 @@ int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t 
   } else {
     HT_CUDA(cudaLaunchKernel(func, dim3((unsigned)grid), dim3(tpb), args, smem, s));
   }
+  return HT_OK;
+}
+
+// Launches the kernel of a shape over units [u_begin, u_end) of the string
+// described by sp (sp.n_items = all units of the string).  digest_dev
+// receives k words when the string's last unit completes.
+int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t u_begin,
+                  uint64_t u_end, uint64_t *digest_dev, cudaStream_t s) {
+  const KernelSet &ks = *c->ks;
+  const void *func = single_func(ks, shape, sp);
+  const size_t smem = shape.kernel == 0 ? stream_smem(ks, shape) : 0;
+  int tpb = shape.threads_per_block;
+  const int occ = occupancy(c, func, tpb, smem);
+  if (occ == 0) return set_error(HT_ERR_ARG, "launch shape does not fit the device");
+  const int bps = std::min(shape.blocks_per_sm, occ);
+  const uint64_t grid = grid_for(c, shape.kernel, u_end - u_begin, bps, &tpb);
+  const bool overlap = (shape.kernel == 1 || shape.kernel == 3) && (c->flags & HT_FLAG_OVERLAP_LAUNCHES);
+  KParams P;
+  fill_keys(c, P);
+  P.single = sp;
+  P.item_begin = u_begin;
+  P.item_end = u_end;
+  P.digests = (unsigned long long *)digest_dev;
+  P.count = 1;
+  P.total_warps = (unsigned)(grid * (uint64_t)(tpb / 32));
+  P.stages = (unsigned)shape.stages;
+  int rc = launch_kernel(func, grid, tpb, smem, P, overlap, s);
+  if (rc) return rc;
   c->launches.fetch_add(1);
   return HT_OK;
 }
@@ -465,7 +475,7 @@ static std::vector<ht_shape> tune_candidates(ht_ctx *c, bool batch) {
       if (only_l2 || occupancy(c, batch ? ks.range_batch : ks.range_single, tpb, 0) < bps) continue;
       cands.push_back(h);
     }
-  if (!batch && ks.block_single)
+  if (!batch && ks.block_single) {
     for (int bps : {1, 2, 3, 4, 6, 8}) {
       ht_shape h = default_shape();
       h.kernel = 3;
@@ -474,6 +484,7 @@ static std::vector<ht_shape> tune_candidates(ht_ctx *c, bool batch) {
       if (occupancy(c, ks.block_single, 256, 0) < bps) continue;
       cands.push_back(h);
     }
+  }
   for (int L : {1, 2, 3})
     for (int tpb : {128, 256})
       for (int bps : {1, 2, 3, 4, 6, 8}) {

@@ -47,9 +47,12 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
 }
 
 // Waits for the phase of `parity` to complete; false after `budget` cycles.
+// The clock is read before every try (a try may itself suspend the thread
+// for a while), so a budget of a few cycles runs out before the first try.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget = kWaitCycles) {
   const long long t0 = clock64();
   for (;;) {
+    if (clock64() - t0 > budget) return false;
     uint32_t done;
     asm volatile(
         "{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
@@ -57,7 +60,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > budget) return false;
   }
 }
 

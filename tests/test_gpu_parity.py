@@ -116,7 +116,7 @@ def _set_all(h, shape):
     """Every length bucket, and the batch shape unless the kernel serves
     single strings only (the block-chunk kernel)."""
     from paper_2104_08865_gb300 import abi
-    for n in [1 << b for b in range(64)] + ([2**64 - 1] if shape["kernel"] != 3 else []):
+    for n in [1 << b for b in range(64)] + ([2**64 - 1] if shape["kernel"] < 3 else []):
         abi.ht_set_shape(h.ctx, n, **shape)
 
 
@@ -287,15 +287,19 @@ def test_rekey_matches_fresh_context(dev, width):
     assert np.array_equal(got, oracle.hash_bytes(width, ref2, data))
 
 
-def test_overlapped_launches_keep_digests(dev):
+@pytest.mark.parametrize("shape", [None, "block-256x2"])
+def test_overlapped_launches_keep_digests(dev, shape):
     """Back-to-back hashes with HT_FLAG_OVERLAP_LAUNCHES (each launch may
     start while the previous one drains) on two contexts sharing one stream,
-    over sizes from empty to several rounds of chunks: every digest equals the
-    oracle's."""
+    over sizes from empty to several rounds of chunks, with the default
+    shapes and with the block-chunk kernel for every length: every digest
+    equals the oracle's."""
     from paper_2104_08865_gb300 import abi
     pairs = [_pair(24, seed=3), _pair(40, seed=4)]
     for h, _ in pairs:
         abi.ht_ctx_set_flags(h.ctx, abi.HT_FLAG_OVERLAP_LAUNCHES)
+        if shape:
+            _set_all(h, SHAPES[shape])
     lens = [0, 17, 5000, 300_000, 9 << 20, (1 << 26) + 12345, 3 << 20, 1 << 27]
     data = inputs.stream_bytes_torch(15, 0, max(lens), dev)
     outs = []
@@ -430,3 +434,31 @@ def test_c3_collision_sweep(dev, width):
     offs = np.arange(10_000, dtype=np.int64) * n
     want = oracle.hash_many(width, ref, host, offs, [n] * 10_000)
     assert np.array_equal(sample, want)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_block_chunk_kernel_interleaved(dev, width):
+    """Strings of 0 to 520 whole 64-execution chunks hashed by the block-chunk
+    kernel (the default below 32 MiB), around each 8^l boundary of the
+    chunk count and with partial chunks and tails, one after another on one
+    context, then again in reverse order: a launch that leaves anything in
+    the scratch spoils the next one."""
+    h, ref = _pair(width, seed=19)
+    xb = oracle.params(width)["exec_bytes"]
+    lens = []
+    for i, c in enumerate([0, 1, 2, 7, 8, 9, 63, 64, 65, 100, 511, 512, 513, 520]):
+        for r in (0, 5, 63):
+            if c * 64 + r:
+                lens.append((c * 64 + r) * xb + (i * 41 + r) % xb)
+    buf, offs = inputs.packed_batch(31, lens)
+    want = oracle.hash_many(width, ref, buf, offs, lens)
+    dbuf = torch.from_numpy(buf).to(dev)
+    for rep in range(2):
+        order = list(range(len(lens))) if rep == 0 else list(range(len(lens)))[::-1]
+        out = torch.empty((len(lens), h.k), dtype=torch.int64, device=dev)
+        for i in order:
+            h.hash(dbuf, int(lens[i]), out=out[i], offset=int(offs[i]))
+        h.status()
+        got = _u64(out)
+        bad = np.nonzero(~np.all(got == want, axis=1))[0]
+        assert bad.size == 0, (rep, [lens[i] // xb for i in bad[:10]])
