@@ -487,7 +487,11 @@ typedef struct ht_shape {
   int blocks_per_sm;     /* 1 .. 32; clamped to the occupancy limit */
 } ht_shape;
 
-/* Times every candidate shape on `len`-byte strings in a device buffer
+/* The candidates are the warp-chunk kernel (chunk heights 1-3, 128 or 256
+ * threads per block, 1-8 blocks per SM) and the block-chunk kernel (1-8
+ * blocks per SM); the stream and hybrid families are selectable with
+ * ht_set_shape but not tuned (on GB300 they won no length and no batch).
+ * Times every candidate shape on `len`-byte strings in a device buffer
  * allocated and freed inside the call (at least 384 MiB, so that short
  * strings are timed from HBM, not from the L2 cache: each launch takes the
  * next copy) and stores the fastest in the bucket of len;
@@ -496,9 +500,10 @@ typedef struct ht_shape {
 int ht_autotune(ht_ctx *ctx, uint64_t len, ht_stream_t stream, ht_shape *best);
 
 /* The same for batches (the persistent kernel of ht_hash_batch): times every
- * candidate batch shape -- kernel family, chunk height L (executions per
- * work item, 8^L: the parallelism a string gets), threads per block and
- * blocks per SM -- on the caller's own batch, and stores the fastest as the
+ * candidate batch shape -- the warp-chunk kernel's chunk height L
+ * (executions per work item, 8^L: the parallelism a string gets), threads
+ * per block and blocks per SM -- on the caller's own batch, and stores the
+ * fastest as the
  * context's batch shape (the one ht_hash_batch and servers created from this
  * context use).  Arguments as for ht_hash_batch; digests_dev receives the
  * batch's digests (from the last run: the same for every shape).  A shape

@@ -445,36 +445,17 @@ int launch_single(ht_ctx *c, const ht_shape &shape, const StrPlan &sp, uint64_t 
   return HT_OK;
 }
 
-// Candidate launch shapes of the three kernel families that fit the device,
-// for single strings or for batches (the warp-chunk kernel with 64-execution
-// items only, for 256-bit blocks and for the binary-tree ablation).
+// Candidate launch shapes that fit the device, for single strings or for
+// batches: the warp-chunk kernel (64-execution items only, for 256-bit
+// blocks and for the binary-tree ablation) and, for single strings, the
+// block-chunk kernel.
 static std::vector<ht_shape> tune_candidates(ht_ctx *c, bool batch) {
   const KernelSet &ks = *c->ks;
-  const bool only_l2 = ks.lanes != kLanes || ks.tree;
   std::vector<ht_shape> cands;
-  for (int warps : {2, 3, 4, 5, 6, 8})
-    for (int stages : {2, 3, 4, 6})
-      for (int bps : {1, 2, 3, 4}) {
-        ht_shape h = default_shape();
-        h.kernel = 0;
-        h.stages = stages;
-        h.threads_per_block = 32 * warps;
-        h.blocks_per_sm = bps;
-        if (only_l2) continue;
-        const size_t smem = stream_smem(ks, h);
-        if ((int)smem > c->smem_optin) continue;
-        if (occupancy(c, batch ? ks.stream_batch : ks.stream_single, h.threads_per_block, smem) < bps) continue;
-        cands.push_back(h);
-      }
-  for (int tpb : {128, 256})
-    for (int bps : {1, 2, 3, 4, 6, 8}) {
-      ht_shape h = default_shape();
-      h.kernel = 2;
-      h.threads_per_block = tpb;
-      h.blocks_per_sm = bps;
-      if (only_l2 || occupancy(c, batch ? ks.range_batch : ks.range_single, tpb, 0) < bps) continue;
-      cands.push_back(h);
-    }
+  // (The stream and hybrid families are not candidates: on GB300 neither won
+  // any length from 64 KiB to 1 GiB at widths 24 and 40, nor the
+  // 50,000-string batch, timed on cold data; ht_set_shape still selects
+  // them.)
   if (!batch && ks.block_single) {
     for (int bps : {1, 2, 3, 4, 6, 8}) {
       ht_shape h = default_shape();
