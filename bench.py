@@ -420,8 +420,9 @@ def run_incremental(args, dev, stream, data, want):
     """The benchmark's string hashed incrementally at width 24 (init / update /
     final): device-resident pieces of 64 MiB and of 1 MiB + 3 bytes (every
     piece boundary inside a chunk, so each update also copies a partial
-    chunk), and pinned host pieces of 64 MiB through the host update.  The
-    digest must equal the one-shot digest."""
+    chunk), both also with overlapping launches (HT_FLAG_OVERLAP_LAUNCHES),
+    and pinned host pieces of 64 MiB through the host update.  The digest
+    must equal the one-shot digest."""
     import numpy as np
     import torch
 
@@ -440,7 +441,12 @@ def run_incremental(args, dev, stream, data, want):
         inc.final(out, stream)
 
     same = True
-    for name, piece, reps in (("device_64mib", 64 << 20, 10), ("device_1mib_plus_3", (1 << 20) + 3, 3)):
+    for name, piece, reps, flags in (("device_64mib", 64 << 20, 10, 0),
+                                     ("device_1mib_plus_3", (1 << 20) + 3, 3, 0),
+                                     ("device_64mib_overlapped", 64 << 20, 10, abi.HT_FLAG_OVERLAP_LAUNCHES),
+                                     ("device_1mib_plus_3_overlapped", (1 << 20) + 3, 3,
+                                      abi.HT_FLAG_OVERLAP_LAUNCHES)):
+        abi.ht_ctx_set_flags(h.ctx, flags)
         run_dev(piece)
         torch.cuda.synchronize()
         same &= out.cpu().numpy().view(np.uint64).tolist() == want
@@ -454,6 +460,7 @@ def run_incremental(args, dev, stream, data, want):
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"gbs": round(n / ms / 1e6, 1), "ms": round(ms, 3),
                      "launches": (h.launches() - l0) // reps}
+    abi.ht_ctx_set_flags(h.ctx, 0)
     pinned = torch.empty(n, dtype=torch.uint8).pin_memory()
     pinned.copy_(data)
     hp = pinned.numpy()

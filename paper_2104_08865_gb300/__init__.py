@@ -186,6 +186,10 @@ class Incremental:
         _abi().ht_inc_final(self.h, out.data_ptr(), self._stream(stream))
         return out
 
+    def status(self, stream=None):
+        """Raises if a checked-build launch of this handle skipped an access."""
+        _abi().ht_inc_status(self.h, self._stream(stream))
+
     def length(self) -> int:
         return _abi().ht_inc_length(self.h)
 

@@ -59,7 +59,9 @@ __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ K
     uint32_t bsh = sh;
     if constexpr (INC) {
       if (P.inc_first && item == sp.chunk0) {
-        // the update's first chunk waits in the handle's buffer
+        // the update's first chunk waits in the handle's buffer, completed
+        // by the kernel before this one
+        griddep_wait();
         base = P.inc_first - item * 64 * XB;
         bsh = ALIGNED ? 0u : (uint32_t)(((uintptr_t)base) & 15u);
       }
@@ -126,6 +128,9 @@ __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ K
   griddep_wait();
   if constexpr (INC) {
     if (blockIdx.x == 0 && w == 0) seed_frontier<W>(P, sp, ln);
+    // the bytes after the last whole chunk, for the next update
+    copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+               (uint64_t)gridDim.x * blockDim.x);
   }
   const bool last = exit_protocol(P, ln);
   if (!INC && last && P.item_end >= sp.n_items) finish_string<W>(P, sp, 0, ln);

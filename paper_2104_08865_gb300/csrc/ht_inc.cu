@@ -6,7 +6,10 @@
 // bytes that do not yet fill a 64-execution chunk.  Updates run the
 // warp-chunk kernel in its incremental mode over whole chunks, straight from
 // the caller's memory; only the bytes that straddle an update boundary are
-// copied.  The final call hashes the stack's pending nodes, the buffered
+// copied (by kernels: the bytes that complete the buffered chunk by a small
+// copy kernel, the update's own remainder by the update kernel, into the
+// handle's other buffer), so that an update is a chain of kernels that may
+// overlap one another.  The final call hashes the stack's pending nodes, the buffered
 // executions and the tail.  The digest equals the one-shot digest of the
 // concatenated pieces.
 #include <cuda_runtime.h>
@@ -65,7 +68,11 @@ struct ht_inc {
   Ctl *ctl = nullptr;
   unsigned long long *stack[2] = {nullptr, nullptr};  // the state and the next update's output
   int cur = 0;            // stack[cur] holds the state
-  uint8_t *buf = nullptr;
+  // bytes short of a whole chunk wait in buf[bcur]; an update's kernel
+  // copies its own remainder into the other buffer (so that it never writes
+  // the buffer it reads its first chunk from)
+  uint8_t *buf[2] = {nullptr, nullptr};
+  int bcur = 0;
   // host mirror of the counter
   uint64_t chunks = 0;  // whole chunks hashed
   uint64_t fill = 0;    // bytes waiting in buf (< granule)
@@ -98,8 +105,11 @@ void inc_params(const ht_inc *h, KParams &P) {
 
 // Hashes chunks [h->chunks, h->chunks + M): the first from the chunk buffer
 // if first_from_buf, the others (or all) contiguous at ptr (device).  One
-// launch; it reads the stack of the state and writes the other one.
-int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, cudaStream_t s) {
+// launch; it reads the stack of the state and writes the other one, and
+// copies rem_len bytes from rem_src into the other chunk buffer (which then
+// becomes the current one).  pdl: launched to overlap the kernel before it.
+int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, cudaStream_t s,
+               const uint8_t *rem_src = nullptr, uint64_t rem_len = 0, bool pdl = false) {
   ht_ctx *c = h->ctx;
   const KernelSet &ks = *c->ks;
   const uint64_t C = h->chunks;
@@ -112,7 +122,10 @@ int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, c
   StrPlan &sp = P.single;
   // the kernel addresses the string from its start
   sp.ptr = ptr - (C + (first_from_buf ? 1 : 0)) * h->granule;
-  if (first_from_buf) P.inc_first = h->buf;
+  if (first_from_buf) P.inc_first = h->buf[h->bcur];
+  P.inc_rem_src = rem_src;
+  P.inc_rem_dst = h->buf[h->bcur ^ 1];
+  P.inc_rem_len = rem_len;
   sp.n_exec = (C + M) * kChunkExecs;
   sp.len = sp.n_exec * (uint64_t)ks.exec_bytes;
   sp.chunk0 = C;
@@ -147,11 +160,45 @@ int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, c
   P.item_begin = C;
   P.item_end = C + M;
   P.total_warps = (unsigned)(grid * wpb);
-  cudaError_t e = cudaLaunchKernel(func, dim3((unsigned)grid), dim3((unsigned)(32 * wpb)), args, 0, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)(32 * wpb));
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, func, args);
   if (e != cudaSuccess) return cuda_error(e, "incremental update launch");
   c->launches.fetch_add(1);
   h->chunks = C + M;
   h->cur ^= 1;
+  if (rem_len) h->bcur ^= 1;
+  return HT_OK;
+}
+
+// Completes the buffered chunk (h->fill bytes in buf[bcur]) with n bytes
+// from src (device) in a kernel, so that the update kernel after it can
+// overlap it.
+int complete_chunk(ht_inc *h, const uint8_t *src, uint64_t n, cudaStream_t s, bool pdl) {
+  ht_ctx *c = h->ctx;
+  uint8_t *dst = h->buf[h->bcur] + h->fill;
+  unsigned long long nn = n;
+  void *args[] = {&dst, &src, &nn};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)std::max<uint64_t>(1, std::min<uint64_t>(64, (n + 4095) / 4096)));
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, c->ks->inc_copy, args);
+  if (e != cudaSuccess) return cuda_error(e, "incremental chunk completion");
+  c->launches.fetch_add(1);
+  h->fill += n;
   return HT_OK;
 }
 
@@ -163,7 +210,8 @@ void free_inc(ht_inc *h) {
   cudaFree(h->ctl);
   cudaFree(h->stack[0]);
   cudaFree(h->stack[1]);
-  cudaFree(h->buf);
+  cudaFree(h->buf[0]);
+  cudaFree(h->buf[1]);
   for (int i = 0; i < kStageSlots2; ++i) {
     cudaFree(h->stage[i]);
     if (h->ev_copy[i]) cudaEventDestroy(h->ev_copy[i]);
@@ -203,7 +251,8 @@ int ht_inc_create(ht_ctx *c, ht_inc **out) {
   alloc((void **)&h->ctl, sizeof(Ctl));
   alloc((void **)&h->stack[0], stack_words(h) * sizeof(unsigned long long));
   alloc((void **)&h->stack[1], stack_words(h) * sizeof(unsigned long long));
-  alloc((void **)&h->buf, h->granule);
+  alloc((void **)&h->buf[0], h->granule);
+  alloc((void **)&h->buf[1], h->granule);
   if (e != cudaSuccess) {
     free_inc(h);
     delete h;
@@ -243,6 +292,7 @@ int ht_inc_init(ht_inc *h, ht_stream_t stream) {
   INC_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s));
   h->chunks = 0;
   h->fill = 0;
+  h->bcur = 0;
   h->open = true;
   return HT_OK;
 }
@@ -262,33 +312,41 @@ int ht_inc_update(ht_inc *h, const void *data_dev, uint64_t len, ht_stream_t str
   if (len > ~0ull - ht_inc_length(h)) return set_error(HT_ERR_TOO_LONG, "ht_inc_update: string longer than 2^64 - 1 bytes");
   cudaStream_t s = (cudaStream_t)stream;
   const uint8_t *p = static_cast<const uint8_t *>(data_dev);
+  const uint64_t G = h->granule;
   uint64_t m = len;
+  if (!m) return HT_OK;
+  if (h->fill + m < G) {
+    // no chunk completes: the bytes join the buffer
+    INC_CUDA(cudaMemcpyAsync(h->buf[h->bcur] + h->fill, p, m, cudaMemcpyDeviceToDevice, s));
+    h->fill += m;
+    return HT_OK;
+  }
+  // a chain of kernels only (the chunk completion, the updates, each
+  // update's remainder copied by the update itself), so that with
+  // HT_FLAG_OVERLAP_LAUNCHES each may overlap the one before it
+  const bool pdl = (h->ctx->flags & HT_FLAG_OVERLAP_LAUNCHES) != 0;
   bool buffered = false;  // the chunk buffer holds a whole chunk for the first launch
   if (h->fill) {
-    // complete the buffered chunk first
-    const uint64_t r = std::min(m, h->granule - h->fill);
-    if (r) INC_CUDA(cudaMemcpyAsync(h->buf + h->fill, p, r, cudaMemcpyDeviceToDevice, s));
-    h->fill += r;
+    const uint64_t r = G - h->fill;
+    const int rc = complete_chunk(h, p, r, s, pdl);
+    if (rc) return rc;
     p += r;
     m -= r;
-    if (h->fill < h->granule) return HT_OK;
     buffered = true;
   }
-  uint64_t M = m / h->granule;
+  uint64_t M = m / G;
+  const uint64_t rem = m - M * G;
   while (buffered || M) {
     const uint64_t piece = std::min(M, kMaxChunks - (buffered ? 1 : 0));
-    const int rc = run_chunks(h, buffered, p, piece + (buffered ? 1 : 0), s);
+    const bool last = piece == M;
+    const int rc = run_chunks(h, buffered, p, piece + (buffered ? 1 : 0), s, last ? p + piece * G : nullptr,
+                              last ? rem : 0, pdl);
     if (rc) return rc;
-    if (buffered) h->fill = 0;
     buffered = false;
-    p += piece * h->granule;
-    m -= piece * h->granule;
+    p += piece * G;
     M -= piece;
   }
-  if (m) {
-    INC_CUDA(cudaMemcpyAsync(h->buf, p, m, cudaMemcpyDeviceToDevice, s));
-    h->fill = m;
-  }
+  h->fill = rem;
   return HT_OK;
 }
 
@@ -303,7 +361,7 @@ int ht_inc_update_host(ht_inc *h, const void *data_host, uint64_t len, ht_stream
   bool buffered = false;  // the chunk buffer holds a whole chunk for the first launch
   if (h->fill) {
     const uint64_t r = std::min(m, h->granule - h->fill);
-    if (r) INC_CUDA(cudaMemcpyAsync(h->buf + h->fill, p, r, cudaMemcpyHostToDevice, s));
+    if (r) INC_CUDA(cudaMemcpyAsync(h->buf[h->bcur] + h->fill, p, r, cudaMemcpyHostToDevice, s));
     h->fill += r;
     p += r;
     m -= r;
@@ -342,12 +400,12 @@ int ht_inc_update_host(ht_inc *h, const void *data_host, uint64_t len, ht_stream
     }
   }
   if (buffered) {
-    const int rc = run_chunks(h, true, h->buf, 1, s);
+    const int rc = run_chunks(h, true, h->buf[h->bcur], 1, s);
     if (rc) return rc;
     h->fill = 0;
   }
   if (m) {
-    INC_CUDA(cudaMemcpyAsync(h->buf, p, m, cudaMemcpyHostToDevice, s));
+    INC_CUDA(cudaMemcpyAsync(h->buf[h->bcur], p, m, cudaMemcpyHostToDevice, s));
     h->fill = m;
   }
   // the caller may reuse its buffer once this returns (copies from pinned
@@ -366,7 +424,7 @@ int ht_inc_final(ht_inc *h, uint64_t *digest_dev, ht_stream_t stream) {
   KParams P;
   inc_params(h, P);
   StrPlan &sp = P.single;
-  sp.ptr = h->buf - C * h->granule;
+  sp.ptr = h->buf[h->bcur] - C * h->granule;
   sp.len = C * h->granule + h->fill;
   sp.n_exec = C * kChunkExecs + h->fill / (uint64_t)ks.exec_bytes;
   sp.chunk0 = C;
@@ -404,7 +462,7 @@ int ht_inc_export(const ht_inc *h, void *state_host, size_t n, ht_stream_t strea
   uint8_t *b = static_cast<uint8_t *>(state_host) + 4 * sizeof(uint64_t);
   INC_CUDA(cudaMemcpyAsync(b, h->stack[h->cur], stack_words(h) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   if (h->fill)
-    INC_CUDA(cudaMemcpyAsync(b + stack_words(h) * sizeof(uint64_t), h->buf, h->fill, cudaMemcpyDeviceToHost, s));
+    INC_CUDA(cudaMemcpyAsync(b + stack_words(h) * sizeof(uint64_t), h->buf[h->bcur], h->fill, cudaMemcpyDeviceToHost, s));
   INC_CUDA(cudaStreamSynchronize(s));
   return HT_OK;
 }
@@ -425,7 +483,7 @@ int ht_inc_import(ht_inc *h, const void *state_host, size_t n, ht_stream_t strea
   const uint8_t *b = static_cast<const uint8_t *>(state_host) + 4 * sizeof(uint64_t);
   INC_CUDA(cudaMemcpyAsync(h->stack[h->cur], b, stack_words(h) * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   if (hd[3])
-    INC_CUDA(cudaMemcpyAsync(h->buf, b + stack_words(h) * sizeof(uint64_t), hd[3], cudaMemcpyHostToDevice, s));
+    INC_CUDA(cudaMemcpyAsync(h->buf[h->bcur], b + stack_words(h) * sizeof(uint64_t), hd[3], cudaMemcpyHostToDevice, s));
   INC_CUDA(cudaStreamSynchronize(s));
   h->chunks = hd[2];
   h->fill = hd[3];

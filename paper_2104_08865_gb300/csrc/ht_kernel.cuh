@@ -125,6 +125,32 @@ __device__ __forceinline__ uint4 ld16(const uint8_t *p, uint32_t sh) {
   return sh == 0 ? ld_stream(p) : ld_unaligned(p, sh);
 }
 
+// Copies n bytes from src to dst (device memory, any alignments), shared by
+// the caller's threads t = 0 .. nt-1: 16-byte stores over the part of dst
+// that is 16-byte aligned (the source read with aligned loads and funnel
+// shifts, touching only the 16-byte granules that hold source bytes), single
+// bytes before and after it.
+__device__ __forceinline__ void copy_bytes(uint8_t *dst, const uint8_t *src, uint64_t n, uint64_t t,
+                                           uint64_t nt) {
+  if (!n) return;
+  const uintptr_t d0 = (uintptr_t)dst, d1 = d0 + n;
+  const uintptr_t a0 = (d0 + 15) & ~(uintptr_t)15, a1 = d1 & ~(uintptr_t)15;
+  if (a0 >= a1) {
+    for (uint64_t i = t; i < n; i += nt) dst[i] = src[i];
+    return;
+  }
+  const uint64_t head = a0 - d0, mid_end = a1 - d0;
+  for (uint64_t i = t; i < head; i += nt) dst[i] = src[i];
+  for (uint64_t i = mid_end + t; i < n; i += nt) dst[i] = src[i];
+  const uint8_t *s = src + head;
+  const uint32_t sh = (uint32_t)((uintptr_t)s & 15u);
+  const uint64_t ng = (a1 - a0) >> 4;
+  for (uint64_t g = t; g < ng; g += nt) {
+    const uint4 v = sh ? ld_unaligned(s + 16 * g, sh) : ld_stream(s + 16 * g);
+    *reinterpret_cast<uint4 *>(dst + head + 16 * g) = v;
+  }
+}
+
 // One little-endian word of the tail holding nb (1..8) bytes starting at p.
 __device__ __forceinline__ uint64_t tail_word(const uint8_t *p, uint32_t nb) {
   if (nb == 8 && (((uintptr_t)p) & 7u) == 0)
@@ -821,7 +847,11 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
     uint64_t v0, v1;
     const uint8_t *base = sp.ptr;
     if constexpr (INC) {
-      if (P.inc_first && item == sp.chunk0) base = P.inc_first - item * G;
+      if (P.inc_first && item == sp.chunk0) {
+        // the buffered chunk was completed by the kernel before this one
+        griddep_wait();
+        base = P.inc_first - item * G;
+      }
     }
     const bool full = chunk_root<W, L, ALIGNED, B>(P, sp, base, item, ln, pend, anyp, v0, v1);
     // everything below touches the scratch: an overlapping launch must first
@@ -836,6 +866,8 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
   griddep_wait();
   if constexpr (INC) {
     if (gw == 0) seed_frontier<W>(P, sp, ln);
+    // the bytes after the last whole chunk, for the next update
+    copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, 32 * gw + ln, 32ull * P.total_warps);
   }
 }
 

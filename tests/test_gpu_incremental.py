@@ -224,3 +224,62 @@ def test_update_longer_than_one_launch(dev):
         inc.update(dbuf[:777])
         inc.update(dbuf[777:])
         assert np.array_equal(_u64(inc.final()), want)
+
+
+@pytest.mark.parametrize("width", WIDTHS)
+def test_overlapped_updates_match_oracle(dev, width):
+    """With HT_FLAG_OVERLAP_LAUNCHES every update kernel (and the kernel that
+    completes the buffered chunk) may start before the one before it has
+    ended; pieces that straddle chunks back to back, without a host
+    synchronisation, and a piece above 32 MiB (the warp-chunk update kernel)
+    still give the oracle's digest, and the handle's status stays clean."""
+    from paper_2104_08865_gb300 import abi
+    h, ref = _pair(width)
+    abi.ht_ctx_set_flags(h.ctx, abi.HT_FLAG_OVERLAP_LAUNCHES)
+    xb = oracle.params(width)["exec_bytes"]
+    gran = 64 * xb
+    big = ((33 << 20) // gran) * gran + 3 * xb + 5
+    straddle = [gran - 1, gran + 1, 2 * gran + 3, 1, gran, 7, 5 * gran - 2]
+    pieces = straddle * 30 + [big] + straddle * 5 + [17 * xb + 9]
+    n = sum(pieces)
+    dbuf = inputs.stream_bytes_torch(28, 0, n, dev)
+    want = oracle.hash_bytes(width, ref, dbuf.cpu().numpy())
+    with h.incremental() as inc:
+        for rep in range(2):
+            inc.init()
+            _feed(inc, dbuf, None, pieces)
+            assert np.array_equal(_u64(inc.final()), want), rep
+        inc.status()
+
+
+def test_overlapped_updates_between_one_shot_hashes(dev):
+    """Overlapping update kernels interleaved with overlapping one-shot hashes
+    of the same context on one stream: both kinds keep their digests."""
+    from paper_2104_08865_gb300 import abi
+    width = 32
+    h, ref = _pair(width)
+    abi.ht_ctx_set_flags(h.ctx, abi.HT_FLAG_OVERLAP_LAUNCHES)
+    gran = 64 * oracle.params(width)["exec_bytes"]
+    pieces = [3 * gran + 11, 5 * gran - 11, 1, 200 * gran + 99, gran - 100, 4000 * gran + 3, 2]
+    n = sum(pieces)
+    dbuf = inputs.stream_bytes_torch(29, 0, n, dev)
+    host = dbuf.cpu().numpy()
+    want = oracle.hash_bytes(width, ref, host)
+    one_shot = [(0, 5 * gran + 1), (gran + 3, 300 * gran), (7, 2 * gran)]
+    want_one = [oracle.hash_bytes(width, ref, host[o:o + m]) for o, m in one_shot]
+    outs = torch.empty((len(pieces), len(one_shot), h.k), dtype=torch.int64, device=dev)
+    with h.incremental() as inc:
+        off = 0
+        for i, p in enumerate(pieces):
+            inc.update(dbuf[off:off + p])
+            off += p
+            for j, (o, m) in enumerate(one_shot):
+                h.hash(dbuf, m, out=outs[i, j], offset=o)
+        got = _u64(inc.final())
+        inc.status()
+    h.status()
+    assert np.array_equal(got, want)
+    all_one = outs.cpu().numpy().view(np.uint64)
+    for i in range(len(pieces)):
+        for j in range(len(one_shot)):
+            assert np.array_equal(all_one[i, j], want_one[j]), (i, j)
