@@ -97,13 +97,9 @@ __device__ __forceinline__ uint4 ld_stream(const uint8_t *p) {
   return v;
 }
 
-// 16 bytes at an address that is not 16-byte aligned (sh = address & 15,
-// 1..15): two aligned loads of the granules the bytes straddle, realigned
-// with funnel shifts.  Both granules hold bytes of the request, so nothing
-// outside the string's 16-byte granules is touched.
-__device__ __forceinline__ uint4 ld_unaligned(const uint8_t *p, uint32_t sh) {
-  const uint8_t *b = p - sh;
-  const uint4 a = ld_stream(b), c = ld_stream(b + 16);
+// Bytes sh .. sh+15 (sh = 1..15) of the 32 bytes a, c (two consecutive
+// aligned granules), by selects on the word offset and a funnel shift.
+__device__ __forceinline__ uint4 realign(const uint4 a, const uint4 c, uint32_t sh) {
   const uint32_t w[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
   uint32_t u[8], v[8];
 #pragma unroll
@@ -119,10 +115,13 @@ __device__ __forceinline__ uint4 ld_unaligned(const uint8_t *p, uint32_t sh) {
   return o;
 }
 
-template <bool ALIGNED>
-__device__ __forceinline__ uint4 ld16(const uint8_t *p, uint32_t sh) {
-  if (ALIGNED) return ld_stream(p);
-  return sh == 0 ? ld_stream(p) : ld_unaligned(p, sh);
+// 16 bytes at an address that is not 16-byte aligned (sh = address & 15,
+// 1..15): two aligned loads of the granules the bytes straddle, realigned.
+// Both granules hold bytes of the request, so nothing outside the string's
+// 16-byte granules is touched.
+__device__ __forceinline__ uint4 ld_unaligned(const uint8_t *p, uint32_t sh) {
+  const uint8_t *b = p - sh;
+  return realign(ld_stream(b), ld_stream(b + 16), sh);
 }
 
 // Copies n bytes from src to dst (device memory, any alignments), shared by
@@ -208,6 +207,31 @@ __device__ __forceinline__ uint64_t combine(int t, const uint64_t (&h)[E]) {
 
 // ---- EHC ------------------------------------------------------------------------
 
+// Realigns the dw granules v[b] of one unaligned execution (sh = 4Q +
+// r8 / 8, 1..15): each thread's 16 bytes start sh bytes into its own granule
+// and run into the next one, which the thread takes from its group
+// neighbour src (that thread sends its own granule, or, if it is the
+// group's first, the next block's granule, or `last` after the last block).
+// Only the neighbour words the shift reaches (0 .. Q) are exchanged.
+template <int Q, int dw>
+__device__ __forceinline__ void realign_group(uint4 (&v)[dw], const uint4 last, int p, unsigned gmask,
+                                              int src, uint32_t r8) {
+#pragma unroll
+  for (int b = 0; b < dw; ++b) {
+    const uint4 out = p == 0 ? (b + 1 < dw ? v[b + 1] : last) : v[b];
+    uint32_t n[4] = {0u, 0u, 0u, 0u};
+    n[0] = __shfl_sync(gmask, out.x, src);
+    if (Q >= 1) n[1] = __shfl_sync(gmask, out.y, src);
+    if (Q >= 2) n[2] = __shfl_sync(gmask, out.z, src);
+    if (Q >= 3) n[3] = __shfl_sync(gmask, out.w, src);
+    const uint32_t w[8] = {v[b].x, v[b].y, v[b].z, v[b].w, n[0], n[1], n[2], n[3]};
+    v[b].x = __funnelshift_r(w[Q], w[Q + 1], r8);
+    v[b].y = __funnelshift_r(w[Q + 1], w[Q + 2], r8);
+    v[b].z = __funnelshift_r(w[Q + 2], w[Q + 3], r8);
+    v[b].w = __funnelshift_r(w[Q + 3], w[Q + 4], r8);
+  }
+}
+
 // One EHC execution for block lanes 2p and 2p+1 (Section 3.3, Section 5.1):
 // Encode (systematic GF(8) code, XOR only), Hash (NH of every encoded word
 // under its own key E[c*3+u]), Combine (y = T h over Z_{2^64}).  Blocks are
@@ -218,8 +242,37 @@ __device__ __forceinline__ void ehc2(const uint8_t *ex, int p, uint32_t sh,
   using S = Spec<W>;
   constexpr int d = S::d, e = S::e, k = S::k, np = e - d, dw = d * kItemWords;
   uint4 v[dw];
+  if (ALIGNED || sh == 0) {
 #pragma unroll
-  for (int b = 0; b < dw; ++b) v[b] = ld16<ALIGNED>(ex + b * (8 * B) + p * 16, sh);
+    for (int b = 0; b < dw; ++b) v[b] = ld_stream(ex + b * (8 * B) + p * 16);
+  } else {
+    // an unaligned execution: every aligned granule it touches is loaded
+    // once, by the thread whose 16 bytes start in it; the granule after a
+    // thread's own is its group neighbour's (p + 1), or, for the group's
+    // last thread, the first one of the next block, loaded by thread 0 of
+    // the group (one more granule past the last block: it still holds the
+    // execution's last sh bytes).  All loads are in flight at once, as in
+    // the aligned case, and the group exchanges granules by shuffles (the
+    // group's threads always run ehc2 together).
+    constexpr int G = B / 2;  // threads per block
+    const int ln = (int)(threadIdx.x & 31);
+    const int g0 = ln & ~(G - 1);
+    const unsigned gmask = ((1u << G) - 1u) << g0;
+    const int src = g0 + ((p + 1) & (G - 1));
+    const uint8_t *a = ex - sh + p * 16;
+#pragma unroll
+    for (int b = 0; b < dw; ++b) v[b] = ld_stream(a + b * (8 * B));
+    const uint4 last = p == 0 ? ld_stream(a + dw * (8 * B)) : make_uint4(0u, 0u, 0u, 0u);
+    // (the word offset sh / 4 as a constant: only the neighbour's words
+    // that the shift reaches are exchanged)
+    const uint32_t r8 = (sh & 3u) * 8u;
+    switch (sh >> 2) {
+      case 0: realign_group<0>(v, last, p, gmask, src, r8); break;
+      case 1: realign_group<1>(v, last, p, gmask, src, r8); break;
+      case 2: realign_group<2>(v, last, p, gmask, src, r8); break;
+      default: realign_group<3>(v, last, p, gmask, src, r8); break;
+    }
+  }
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
     uint32_t lo[dw], hi[dw];
@@ -417,7 +470,7 @@ __device__ __forceinline__ bool chunk_root(const KParams &P, const StrPlan &sp, 
       if (cnt == 8) {
         // eight leaves -> one level-1 node per (tree, lane), in registers;
         // two executions per iteration keep two loads batches in flight
-#pragma unroll 2
+#pragma unroll (ALIGNED ? 2 : 1)
         for (int s = 0; s < 8; ++s) {
           uint64_t y[2][k];
           if (kChecked && !HT_IN_RANGE(P, kChkInput, (sb + 8ull * x + s + 1) * XB - 1, sp.len)) continue;
