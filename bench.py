@@ -486,6 +486,45 @@ def run_incremental(args, dev, stream, data, want):
     return res
 
 
+def run_unaligned(args, stream, data, hashers, shapes, per_w):
+    """The benchmark string 3 bytes past a 16-byte boundary (its bytes 3 ..
+    n - 14, the same launch shape as the aligned string): each width timed
+    alone as in the aligned per-launch figures."""
+    import torch
+
+    from paper_2104_08865_gb300 import abi
+    nbytes = args.bytes
+    off, n = 3, args.bytes - 16
+    outs = {w: torch.empty(w // 8, dtype=torch.int64, device=data.device) for w in WIDTHS}
+    for w in WIDTHS:
+        sh = shapes[str(w)]
+        abi.ht_set_shape(hashers[w].ctx, n, sh["kernel"], sh["chunk_levels"], sh["stages"],
+                         sh["threads_per_block"], sh["blocks_per_sm"])
+
+    def once(evs=None):
+        for i, w in enumerate(WIDTHS):
+            if evs is not None:
+                evs[i][0].record(stream)
+            abi.ht_hash(hashers[w].ctx, data.data_ptr() + off, n, outs[w].data_ptr(), stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(max(1, args.warmup)):
+        once()
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in WIDTHS]
+           for _ in range(5)]
+    for ev in evs:
+        once(ev)
+    torch.cuda.synchronize()
+    gbs = {}
+    for i, w in enumerate(WIDTHS):
+        ms = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for ev in evs)
+        gbs[str(w)] = round(n / (ms / 1e3) / 1e9, 1)
+    return {"offset": off, "bytes": n, "per_width_gbs": gbs,
+            "vs_aligned": {str(w): round(gbs[str(w)] / (nbytes / (per_w[w] / 1e3) / 1e9), 3)
+                           for w in WIDTHS}}
+
+
 def run_v3(args, dev, stream, data):
     """The 256-bit-block variant (blocks of 4 words, width | HT_BLOCK_256) on the
     benchmark string: each width timed alone (CUDA events around each launch,
@@ -782,6 +821,7 @@ def run_gpu(args):
     per_w = {}
     for i, w in enumerate(WIDTHS):
         per_w[w] = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for ev in solo)
+    unaligned = run_unaligned(args, stream, data, hashers, shapes, per_w) if rank == 0 else None
     # the timed step: the four launches back to back; with overlap on, each
     # launch may start while the previous one drains (its input is never the
     # previous launch's output)
@@ -895,6 +935,7 @@ def run_gpu(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "per_width_gbs": {str(w): round(nbytes / (per_w[w] / 1e3) / 1e9, 2) for w in WIDTHS},
             "per_width_note": "each launch alone, bracketed by CUDA events (no overlap)",
+            "unaligned": unaligned,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "%s<%d> (single string)" % (

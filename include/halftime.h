@@ -325,12 +325,13 @@ int ht_inc_init(ht_inc *h, ht_stream_t stream);
 
 /* Appends len bytes at data_dev (device, any alignment) to the string.
  * Asynchronous: data_dev must stay valid until `stream` reaches this point.
- * An update that completes a chunk is a chain of kernels only (the bytes
- * that complete the buffered chunk, then the update, which also carries its
- * own remainder over into the handle's other buffer); in a context with
- * HT_FLAG_OVERLAP_LAUNCHES each of them overlaps the kernel before it, under
- * the same rule as single-string launches (data_dev not written by the
- * kernel launched just before the call).  Errors: HT_ERR_ARG (no open string, NULL data), HT_ERR_TOO_LONG (total
+ * An update that completes a chunk is one kernel launch (two or more above
+ * 65536 chunks): it reads the chunk begun by earlier updates from the
+ * handle's buffer and from its own first bytes, and carries its own
+ * remainder over into the handle's other buffer.  In a context with
+ * HT_FLAG_OVERLAP_LAUNCHES it overlaps the kernel before it, under the same
+ * rule as single-string launches (data_dev not written by the kernel
+ * launched just before the call).  Errors: HT_ERR_ARG (no open string, NULL data), HT_ERR_TOO_LONG (total
  * length would exceed 2^64 - 1), HT_ERR_CUDA. */
 int ht_inc_update(ht_inc *h, const void *data_dev, uint64_t len, ht_stream_t stream);
 

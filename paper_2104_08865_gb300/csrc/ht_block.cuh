@@ -20,7 +20,14 @@ namespace ht {
 
 // INC: one update of an incremental handle (whole chunks only, the first
 // possibly from the handle's buffer; pending nodes go to the stack, nothing
-// is finished), as the warp-chunk kernel's incremental mode does it.
+// is finished), as the warp-chunk kernel's incremental mode does it.  If the
+// buffer holds only the first P.inc_fill bytes of that chunk (the rest
+// start the update), block 0, whose first item it is, reads each of the
+// chunk's executions from where its bytes are: the buffer, the update, or,
+// for the one execution across the boundary, a copy in shared memory made
+// by the block.  So no other kernel has to complete the chunk first.  The
+// grid's last block only seeds the frontier groups from the previous
+// stack, beside the chunk blocks instead of after one of them.
 template <int W, bool ALIGNED, bool INC = false>
 __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ KParams P) {
   constexpr int k = Spec<W>::k;
@@ -32,17 +39,21 @@ __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ K
   const StrPlan &sp = P.single;
   const uint64_t N = sp.n_exec;
   const uint32_t sh = ALIGNED ? 0u : (uint32_t)(((uintptr_t)sp.ptr) & 15u);
+  // blocks that take chunks (an incremental update's last block seeds the
+  // frontier instead)
+  const unsigned nb = INC ? gridDim.x - 1 : gridDim.x;
   griddep_launch_dependents();
   bool first = true;
   for (;;) {
     uint64_t item;
     if (first) {
+      if (INC && blockIdx.x == nb) break;
       item = P.item_begin + blockIdx.x;
       first = false;
     } else {
-      if (P.item_end - P.item_begin <= gridDim.x) break;  // one round: nothing left to hand out
+      if (P.item_end - P.item_begin <= nb) break;  // one round: nothing left to hand out
       __syncthreads();  // warp 0 is done with the previous chunk's nodes
-      if (threadIdx.x == 0) s_item = atomicAdd(&P.scr.ctl->cursor, 1ull) + P.item_begin + gridDim.x;
+      if (threadIdx.x == 0) s_item = atomicAdd(&P.scr.ctl->cursor, 1ull) + P.item_begin + nb;
       __syncthreads();
       item = s_item;
     }
@@ -55,20 +66,44 @@ __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ K
     const uint64_t sb = e0 + 8ull * w;  // this warp's eight executions
     const int m = sb >= N ? 0 : (int)((N - sb) < 8 ? (N - sb) : 8);
     const int M = e0 >= N ? 0 : (int)((N - e0) < 64 ? (N - e0) : 64);  // executions of the chunk
-    const uint8_t *base = sp.ptr;
-    uint32_t bsh = sh;
+    const uint8_t *ex = sp.ptr + (sb + (uint64_t)x) * XB;  // this thread's execution
+    uint32_t esh = sh;
+    bool generic = false;  // ex is a generic (shared-memory) address
     if constexpr (INC) {
       if (P.inc_first && item == sp.chunk0) {
-        // the update's first chunk waits in the handle's buffer, completed
-        // by the kernel before this one
+        // the update's first chunk: its first bytes were left in the handle's
+        // buffer by the kernel before this one
         griddep_wait();
-        base = P.inc_first - item * 64 * XB;
-        bsh = ALIGNED ? 0u : (uint32_t)(((uintptr_t)base) & 15u);
+        const uint64_t e = 8ull * w + (uint64_t)x;  // the execution in the chunk
+        if (!P.inc_fill) {
+          ex = P.inc_first + e * XB;  // completed by a kernel before this one
+          esh = 0;
+        } else if constexpr (!ALIGNED) {
+          __shared__ __align__(16) uint4 across[XB / 16];  // the execution across the boundary
+          const uint64_t fill = P.inc_fill;
+          const uint8_t *src = reinterpret_cast<const uint8_t *>(P.inc_stage_src);  // chunk byte fill
+          const uint64_t ea = fill / XB;
+          // (one granule per thread: XB / 16 <= 84 < 256)
+          if (fill % XB && threadIdx.x < XB / 16)
+            across[threadIdx.x] = chunk_granule(P.inc_first, src, fill, ea * XB + 16ull * threadIdx.x);
+          __syncthreads();
+          if ((e + 1) * XB <= fill) {
+            ex = P.inc_first + e * XB;
+            esh = 0;
+          } else if (e * XB >= fill) {
+            ex = src + (e * XB - fill);
+            esh = (uint32_t)((uintptr_t)ex & 15u);
+          } else {
+            ex = reinterpret_cast<const uint8_t *>(across);
+            esh = 0;
+            generic = true;
+          }
+        }
       }
     }
     uint64_t y[2][k];
     if (x < m && HT_IN_RANGE(P, kChkInput, (sb + x + 1) * XB - 1, sp.len))
-      ehc2<W, ALIGNED>(base + (sb + (uint64_t)x) * XB, p, bsh, P, y);
+      ehc2<W, ALIGNED>(ex, p, esh, P, y, INC && generic);
     if (m == 8) {
       // level 1 across the eight x-threads; thread x = t keeps tree t: into
       // shared memory for level 2, or, in the string's last, incomplete
@@ -127,7 +162,7 @@ __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ K
   }
   griddep_wait();
   if constexpr (INC) {
-    if (blockIdx.x == 0 && w == 0) seed_frontier<W>(P, sp, ln);
+    if (blockIdx.x == nb && w == 0) seed_frontier<W>(P, sp, ln);
     // the bytes after the last whole chunk, for the next update
     copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                (uint64_t)gridDim.x * blockDim.x);

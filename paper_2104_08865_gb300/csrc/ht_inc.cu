@@ -5,11 +5,11 @@
 // 5.2: the pending nodes of every level, kept on a stack) and a buffer for
 // bytes that do not yet fill a 64-execution chunk.  Updates run the
 // warp-chunk kernel in its incremental mode over whole chunks, straight from
-// the caller's memory; only the bytes that straddle an update boundary are
-// copied (by kernels: the bytes that complete the buffered chunk by a small
-// copy kernel, the update's own remainder by the update kernel, into the
-// handle's other buffer), so that an update is a chain of kernels that may
-// overlap one another.  The final call hashes the stack's pending nodes, the buffered
+// the caller's memory; only the bytes after an update's last whole chunk
+// are copied (by the update kernel itself, into the handle's other buffer),
+// and the next update reads its first chunk from the buffer and from its
+// own first bytes, so that an update is one kernel that may overlap the one
+// before it.  The final call hashes the stack's pending nodes, the buffered
 // executions and the tail.  The digest equals the one-shot digest of the
 // concatenated pieces.
 #include <cuda_runtime.h>
@@ -103,13 +103,25 @@ void inc_params(const ht_inc *h, KParams &P) {
   P.count = 1;
 }
 
+// Updates of fewer bytes than this run the block-chunk kernel (a block of
+// eight warps per chunk, one execution per thread; its block for the first
+// chunk reads it with 256 threads).  Measured on GB300 (width 24, pieces
+// back to back with overlapping launches): 64 MiB + 3 bytes 25.6 us per
+// update against 27.1 with the warp-chunk kernel, 128 MiB + 3 bytes 41.4
+// against 33.4.
+constexpr uint64_t kBlockwiseBytes = 96ull << 20;
+
 // Hashes chunks [h->chunks, h->chunks + M): the first from the chunk buffer
 // if first_from_buf, the others (or all) contiguous at ptr (device).  One
 // launch; it reads the stack of the state and writes the other one, and
 // copies rem_len bytes from rem_src into the other chunk buffer (which then
-// becomes the current one).  pdl: launched to overlap the kernel before it.
+// becomes the current one).  fill > 0: the buffer holds only the first
+// fill bytes of the first chunk, and the launch reads its other G - fill
+// bytes where they are, before ptr.  pdl: launched to overlap the kernel
+// before it.
 int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, cudaStream_t s,
-               const uint8_t *rem_src = nullptr, uint64_t rem_len = 0, bool pdl = false) {
+               const uint8_t *rem_src = nullptr, uint64_t rem_len = 0, bool pdl = false,
+               uint64_t fill = 0) {
   ht_ctx *c = h->ctx;
   const KernelSet &ks = *c->ks;
   const uint64_t C = h->chunks;
@@ -123,6 +135,9 @@ int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, c
   // the kernel addresses the string from its start
   sp.ptr = ptr - (C + (first_from_buf ? 1 : 0)) * h->granule;
   if (first_from_buf) P.inc_first = h->buf[h->bcur];
+  P.inc_fill = first_from_buf ? fill : 0;
+  // (the update's first G - fill bytes end where the chunks at ptr begin)
+  P.inc_stage_src = (unsigned long long)(uintptr_t)(ptr - (h->granule - fill));
   P.inc_rem_src = rem_src;
   P.inc_rem_dst = h->buf[h->bcur ^ 1];
   P.inc_rem_len = rem_len;
@@ -131,25 +146,26 @@ int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, c
   sp.chunk0 = C;
   sp.n_items = 0xffffffffu;
   void *args[] = {&P};
-  const bool aligned = (((uintptr_t)sp.ptr) & 15u) == 0;
-  // updates below 32 MiB: the block-chunk kernel (a block of eight warps
-  // per chunk, one execution per thread), as for one-shot strings
-  const bool blockwise = M * h->granule < (32ull << 20);
+  // (a partial buffered chunk takes the update's first bytes at any
+  // alignment: the general kernel)
+  const bool aligned = (((uintptr_t)sp.ptr) & 15u) == 0 && !P.inc_fill;
+  const bool blockwise = M * h->granule < kBlockwiseBytes;
   const void *func = blockwise ? (aligned ? ks.inc_block_aligned : ks.inc_block_unaligned)
                                : (aligned ? ks.inc_aligned : ks.inc_unaligned);
   const int bps = 2;  // (both kernels fit two blocks of 256 threads per SM)
   uint64_t wpb = kTpb / 32, grid;
   if (blockwise) {
-    // one chunk per block, whole rounds of blocks
+    // one chunk per block, whole rounds of blocks, and one more block that
+    // seeds the frontier
     const uint64_t bmax = (uint64_t)c->num_sms * bps;
     const uint64_t rounds = (M + bmax - 1) / bmax;
-    grid = (M + rounds - 1) / rounds;
+    grid = (M + rounds - 1) / rounds + 1;
   } else {
     // whole rounds of cursor grabs (see the one-shot launch), one round
-    // spread over every SM
+    // spread over every SM, and one more warp that seeds the frontier
     const uint64_t wmax = (uint64_t)c->num_sms * bps * wpb;
     const uint64_t rounds = (M + wmax - 1) / wmax;
-    const uint64_t warps = (M + rounds - 1) / rounds;
+    const uint64_t warps = (M + rounds - 1) / rounds + 1;
     grid = std::max<uint64_t>(1, (warps + wpb - 1) / wpb);
     if (rounds == 1 && grid < (uint64_t)c->num_sms) {
       wpb = std::max<uint64_t>(1, warps / (uint64_t)c->num_sms);
@@ -175,30 +191,6 @@ int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, c
   h->chunks = C + M;
   h->cur ^= 1;
   if (rem_len) h->bcur ^= 1;
-  return HT_OK;
-}
-
-// Completes the buffered chunk (h->fill bytes in buf[bcur]) with n bytes
-// from src (device) in a kernel, so that the update kernel after it can
-// overlap it.
-int complete_chunk(ht_inc *h, const uint8_t *src, uint64_t n, cudaStream_t s, bool pdl) {
-  ht_ctx *c = h->ctx;
-  uint8_t *dst = h->buf[h->bcur] + h->fill;
-  unsigned long long nn = n;
-  void *args[] = {&dst, &src, &nn};
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)std::max<uint64_t>(1, std::min<uint64_t>(64, (n + 4095) / 4096)));
-  cfg.blockDim = dim3(256);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
-  cudaError_t e = cudaLaunchKernelExC(&cfg, c->ks->inc_copy, args);
-  if (e != cudaSuccess) return cuda_error(e, "incremental chunk completion");
-  c->launches.fetch_add(1);
-  h->fill += n;
   return HT_OK;
 }
 
@@ -321,18 +313,17 @@ int ht_inc_update(ht_inc *h, const void *data_dev, uint64_t len, ht_stream_t str
     h->fill += m;
     return HT_OK;
   }
-  // a chain of kernels only (the chunk completion, the updates, each
-  // update's remainder copied by the update itself), so that with
-  // HT_FLAG_OVERLAP_LAUNCHES each may overlap the one before it
+  // kernels only (each update's remainder copied by the update itself), so
+  // that with HT_FLAG_OVERLAP_LAUNCHES each may overlap the one before it
   const bool pdl = (h->ctx->flags & HT_FLAG_OVERLAP_LAUNCHES) != 0;
-  bool buffered = false;  // the chunk buffer holds a whole chunk for the first launch
-  if (h->fill) {
-    const uint64_t r = G - h->fill;
-    const int rc = complete_chunk(h, p, r, s, pdl);
-    if (rc) return rc;
-    p += r;
-    m -= r;
-    buffered = true;
+  // the first launch reads the partial chunk from the buffer and from the
+  // update's first bytes
+  const bool buffered0 = h->fill != 0;
+  bool buffered = buffered0;
+  const uint64_t fill = h->fill;
+  if (buffered0) {
+    p += G - fill;
+    m -= G - fill;
   }
   uint64_t M = m / G;
   const uint64_t rem = m - M * G;
@@ -340,7 +331,7 @@ int ht_inc_update(ht_inc *h, const void *data_dev, uint64_t len, ht_stream_t str
     const uint64_t piece = std::min(M, kMaxChunks - (buffered ? 1 : 0));
     const bool last = piece == M;
     const int rc = run_chunks(h, buffered, p, piece + (buffered ? 1 : 0), s, last ? p + piece * G : nullptr,
-                              last ? rem : 0, pdl);
+                              last ? rem : 0, pdl, buffered ? fill : 0);
     if (rc) return rc;
     buffered = false;
     p += piece * G;

@@ -51,15 +51,4 @@ __global__ void __launch_bounds__(32) inc_stack_kernel(const __grid_constant__ K
     atomicAdd(P.scr.str_acc + x, (unsigned long long)s);
 }
 
-// Completes an incremental handle's buffered chunk with the first n bytes
-// of an update, once the kernel before it in the stream (the previous
-// update, which left the buffered bytes) has finished.  (W only gives each
-// width's table its own instance.)
-template <int W>
-__global__ void __launch_bounds__(256) inc_copy_kernel(uint8_t *dst, const uint8_t *src, unsigned long long n) {
-  griddep_launch_dependents();
-  griddep_wait();
-  copy_bytes(dst, src, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
-}
-
 }  // namespace ht

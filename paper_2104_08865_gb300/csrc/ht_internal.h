@@ -73,6 +73,8 @@ struct KParams {
   unsigned long long *stack;    // incremental mode: pending nodes [level][8][k][8] (written)
   const unsigned long long *stack_in;  // incremental mode: the previous update's stack (read)
   const uint8_t *inc_first;     // incremental mode: bytes of chunk chunk0 if not at ptr (else null)
+  unsigned long long inc_fill;  // block-chunk update: only this many bytes of it are at inc_first
+  unsigned long long inc_stage_src;  // ... and the rest start the update, at this address
   // incremental mode: the bytes after the update's last whole chunk, which
   // the kernel copies into the handle's other buffer for the next update
   const uint8_t *inc_rem_src;
@@ -140,7 +142,6 @@ struct KernelSet {
   const void *inc_block_aligned;    // the same with the block-chunk kernel (short updates)
   const void *inc_block_unaligned;
   const void *inc_stack;      // incremental: pending stack nodes into the sum
-  const void *inc_copy;       // incremental: completes the buffered chunk
   const void *wait_probe;     // a bounded wait that runs out (tests the timeout path)
   int exec_bytes, k, n_seed, off_T, off_F, off_R, ew;
   // words per block: 8, or 4 for the 256-bit-block variant, whose set holds

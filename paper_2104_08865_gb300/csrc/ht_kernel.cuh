@@ -150,6 +150,27 @@ __device__ __forceinline__ void copy_bytes(uint8_t *dst, const uint8_t *src, uin
   }
 }
 
+// 16 bytes at byte c (a multiple of 16) of an incremental update's first
+// chunk, whose first `fill` bytes are in the handle's buffer and whose
+// others start the update at src (any alignment): from either place, or,
+// for the granule across the boundary, byte by byte.  (Not inlined: its
+// registers stay out of the kernel's chunk loop.)
+static __device__ __noinline__ uint4 chunk_granule(const uint8_t *buf, const uint8_t *src, uint64_t fill, uint64_t c) {
+  if (c + 16 <= fill) return ld_stream(buf + c);
+  if (c >= fill) {
+    const uint8_t *q = src + (c - fill);
+    const uint32_t qs = (uint32_t)((uintptr_t)q & 15u);
+    return qs ? ld_unaligned(q, qs) : ld_stream(q);
+  }
+  uint32_t wd[4] = {0u, 0u, 0u, 0u};
+  for (uint32_t b = 0; b < 16; ++b) {
+    const uint64_t cb = c + b;
+    const uint32_t byte = cb < fill ? __ldg(buf + cb) : __ldg(src + (cb - fill));
+    wd[b >> 2] |= byte << (8 * (b & 3));
+  }
+  return make_uint4(wd[0], wd[1], wd[2], wd[3]);
+}
+
 // One little-endian word of the tail holding nb (1..8) bytes starting at p.
 __device__ __forceinline__ uint64_t tail_word(const uint8_t *p, uint32_t nb) {
   if (nb == 8 && (((uintptr_t)p) & 7u) == 0)
@@ -238,13 +259,17 @@ __device__ __forceinline__ void realign_group(uint4 (&v)[dw], const uint4 last, 
 // B words (8 B bytes) long.
 template <int W, bool ALIGNED, int B = kLanes>
 __device__ __forceinline__ void ehc2(const uint8_t *ex, int p, uint32_t sh,
-                                     const KParams &P, uint64_t (&y)[2][Spec<W>::k]) {
+                                     const KParams &P, uint64_t (&y)[2][Spec<W>::k], bool generic = false) {
   using S = Spec<W>;
   constexpr int d = S::d, e = S::e, k = S::k, np = e - d, dw = d * kItemWords;
   uint4 v[dw];
   if (ALIGNED || sh == 0) {
+    // (generic: ex is a generic address, e.g. of shared memory, read with
+    // plain loads)
 #pragma unroll
-    for (int b = 0; b < dw; ++b) v[b] = ld_stream(ex + b * (8 * B) + p * 16);
+    for (int b = 0; b < dw; ++b)
+      v[b] = generic ? *reinterpret_cast<const uint4 *>(ex + b * (8 * B) + p * 16)
+                     : ld_stream(ex + b * (8 * B) + p * 16);
   } else {
     // an unaligned execution: every aligned granule it touches is loaded
     // once, by the thread whose 16 bytes start in it; the granule after a
@@ -865,6 +890,65 @@ __device__ void seed_frontier(const KParams &P, const StrPlan &sp, int ln) {
   }
 }
 
+// The level-2 root of an incremental update's first chunk (complete: 64
+// executions) when the handle's buffer holds only its first `fill` bytes
+// and the others start the update at src: thread (x, p) hashes executions
+// 8x .. 8x+7, each read where its bytes are (the buffer, the update at any
+// alignment, or, for the execution across the boundary, a copy the warp
+// makes in shared memory), and the levels are formed as chunk_root does for
+// a full chunk.  Returns the root's lanes 2p, 2p+1 of tree x in v0, v1.
+template <int W>
+__device__ __forceinline__ void inc_chunk0_root(const KParams &P, const uint8_t *buf, uint64_t fill,
+                                                const uint8_t *src, int ln, uint64_t &v0, uint64_t &v1) {
+  constexpr int k = Spec<W>::k;
+  constexpr uint64_t XB = Dims<W>::exec_bytes;
+  __shared__ __align__(16) uint4 across[XB / 16];  // (one warp per block uses it)
+  const int x = ln >> 2, p = ln & 3;
+  const uint64_t ea = fill / XB;
+  if (fill % XB)
+    for (uint32_t g = (uint32_t)ln; g < XB / 16; g += 32) across[g] = chunk_granule(buf, src, fill, ea * XB + 16ull * g);
+  __syncwarp();
+  uint64_t n1[2][k];
+#pragma unroll
+  for (int l = 0; l < 2; ++l)
+#pragma unroll
+    for (int t = 0; t < k; ++t) n1[l][t] = 0;
+#pragma unroll 1
+  for (int s = 0; s < 8; ++s) {
+    const uint64_t e = 8ull * x + s;
+    const uint8_t *ex;
+    uint32_t esh = 0;
+    bool generic = false;
+    if ((e + 1) * XB <= fill) {
+      ex = buf + e * XB;
+    } else if (e * XB >= fill) {
+      ex = src + (e * XB - fill);
+      esh = (uint32_t)((uintptr_t)ex & 15u);
+    } else {
+      ex = reinterpret_cast<const uint8_t *>(across);
+      generic = true;
+    }
+    uint64_t y[2][k];
+    ehc2<W, false>(ex, p, esh, P, y, generic);
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+#pragma unroll
+      for (int t = 0; t < k; ++t) n1[l][t] += (s < 7) ? nh64(y[l][t], P.T0[t][s]) : y[l][t];
+  }
+  v0 = 0;
+  v1 = 0;
+#pragma unroll
+  for (int t = 0; t < k; ++t) {
+    const uint64_t key = x < 7 ? tree_key<W>(P, t, 1, x) : 0;
+    const uint64_t a0 = x_sum(x < 7 ? nh64(n1[0][t], key) : n1[0][t]);
+    const uint64_t a1 = x_sum(x < 7 ? nh64(n1[1][t], key) : n1[1][t]);
+    if (x == t) {
+      v0 = a0;
+      v1 = a1;
+    }
+  }
+}
+
 // A warp's share of one string (single-string launches, incremental updates):
 // chunks from the cursor, each root climbing as far as this warp completes
 // groups.  Completion of the string needs no count per chunk (a fence and an
@@ -878,19 +962,23 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
   constexpr int k = Spec<W>::k;
   constexpr uint64_t G = (1ull << (3 * L)) * Dims<W>::exec_bytes;
   const StrPlan &sp = P.single;
+  // warps that take chunks (an incremental update's last warp seeds the
+  // frontier instead, beside them)
+  const uint64_t cw = INC ? P.total_warps - 1 : P.total_warps;
   bool first = true;
   for (;;) {
     unsigned long long item = 0;
     if (first) {
       // each warp's first chunk is fixed, so it can be hashed before an
       // overlapping launch's predecessor has finished with the scratch
+      if (INC && gw == cw) break;
       item = P.item_begin + gw;
       first = false;
     } else {
       // a launch of one round hands nothing out through the cursor
-      if (P.item_end - P.item_begin <= P.total_warps) break;
+      if (P.item_end - P.item_begin <= cw) break;
       if (ln == 0) item = atomicAdd(&P.scr.ctl->cursor, 1ull);
-      item = __shfl_sync(kFull, item, 0) + P.item_begin + P.total_warps;
+      item = __shfl_sync(kFull, item, 0) + P.item_begin + cw;
     }
     if (item >= P.item_end) break;
     uint64_t pend[k];  // this thread's share of the final-NH sum
@@ -899,14 +987,24 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
     bool anyp = false;
     uint64_t v0, v1;
     const uint8_t *base = sp.ptr;
+    bool full;
+    bool done = false;  // the root is formed (the update's first chunk, read from two places)
     if constexpr (INC) {
       if (P.inc_first && item == sp.chunk0) {
-        // the buffered chunk was completed by the kernel before this one
+        // the update's first chunk: its first bytes were left in the
+        // handle's buffer by the kernel before this one
         griddep_wait();
-        base = P.inc_first - item * G;
+        if (!P.inc_fill) {
+          base = P.inc_first - item * G;  // completed by a kernel before this one
+        } else if constexpr (!ALIGNED) {
+          inc_chunk0_root<W>(P, P.inc_first, P.inc_fill, reinterpret_cast<const uint8_t *>(P.inc_stage_src), ln,
+                             v0, v1);
+          full = true;
+          done = true;
+        }
       }
     }
-    const bool full = chunk_root<W, L, ALIGNED, B>(P, sp, base, item, ln, pend, anyp, v0, v1);
+    if (!done) full = chunk_root<W, L, ALIGNED, B>(P, sp, base, item, ln, pend, anyp, v0, v1);
     // everything below touches the scratch: an overlapping launch must first
     // see its predecessor finish
     griddep_wait();
@@ -918,7 +1016,7 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
   }
   griddep_wait();
   if constexpr (INC) {
-    if (gw == 0) seed_frontier<W>(P, sp, ln);
+    if (gw == cw) seed_frontier<W>(P, sp, ln);
     // the bytes after the last whole chunk, for the next update
     copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, 32 * gw + ln, 32ull * P.total_warps);
   }

@@ -287,7 +287,6 @@ KernelSet make_kernel_set() {
   ks.inc_block_aligned = (const void *)block_kernel<W, true, true>;
   ks.inc_block_unaligned = (const void *)block_kernel<W, false, true>;
   ks.inc_stack = (const void *)inc_stack_kernel<W>;
-  ks.inc_copy = (const void *)inc_copy_kernel<W>;
   ks.wait_probe = (const void *)wait_probe_kernel<W>;
   ks.exec_bytes = Dims<W>::exec_bytes;
   ks.k = Spec<W>::k;
