@@ -124,9 +124,10 @@ int read_status(Ctl *ctl, cudaStream_t s) {
   HT_CUDA(cudaMemset(&ctl->status, 0, sizeof st));
   if (st & kStatusBounds) {
     static const char *const names[] = {"?", "input", "tree keys", "final-NH keys", "tail keys",
-                                        "tree-group slot", "string slot", "digest row", "stack slot"};
+                                        "tree-group slot", "string slot", "digest row", "stack slot",
+                                        "chunk buffer"};
     return set_error(HT_ERR_DEVICE, "checked build: an access outside its buffer was skipped (%s, index %llu)",
-                     names[kind < 9 ? kind : 0], index);
+                     names[kind < 10 ? kind : 0], index);
   }
   if (st & kStatusTooLong)
     return set_error(HT_ERR_TOO_LONG, "a batch exceeded the reserved scratch (no digests written)");

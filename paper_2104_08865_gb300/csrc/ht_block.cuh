@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ K
     bool anyp = false;
     const uint64_t e0 = item * 64;
     const uint64_t sb = e0 + 8ull * w;  // this warp's eight executions
-    const int m = sb >= N ? 0 : (int)((N - sb) < 8 ? (N - sb) : 8);
+    int m = sb >= N ? 0 : (int)((N - sb) < 8 ? (N - sb) : 8);
     const int M = e0 >= N ? 0 : (int)((N - e0) < 64 ? (N - e0) : 64);  // executions of the chunk
     const uint8_t *ex = sp.ptr + (sb + (uint64_t)x) * XB;  // this thread's execution
     uint32_t esh = sh;
@@ -80,7 +80,10 @@ __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ K
           esh = 0;
         } else if constexpr (!ALIGNED) {
           __shared__ __align__(16) uint4 across[XB / 16];  // the execution across the boundary
-          const uint64_t fill = P.inc_fill;
+          // (the buffer holds fewer bytes than a chunk; else nothing of the
+          // chunk is read)
+          const uint64_t fill = HT_IN_RANGE(P, kChkIncBuf, P.inc_fill, 64 * XB) ? P.inc_fill : 0;
+          if (!fill) m = 0;
           const uint8_t *src = reinterpret_cast<const uint8_t *>(P.inc_stage_src);  // chunk byte fill
           const uint64_t ea = fill / XB;
           // (one granule per thread: XB / 16 <= 84 < 256)
@@ -164,8 +167,9 @@ __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ K
   if constexpr (INC) {
     if (blockIdx.x == nb && w == 0) seed_frontier<W>(P, sp, ln);
     // the bytes after the last whole chunk, for the next update
-    copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-               (uint64_t)gridDim.x * blockDim.x);
+    if (HT_IN_RANGE(P, kChkIncBuf, P.inc_rem_len, 64 * XB))
+      copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                 (uint64_t)gridDim.x * blockDim.x);
   }
   const bool last = exit_protocol(P, ln);
   if (!INC && last && P.item_end >= sp.n_items) finish_string<W>(P, sp, 0, ln);

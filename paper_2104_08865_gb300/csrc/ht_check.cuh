@@ -29,6 +29,7 @@ enum CheckKind : unsigned int {
   kChkString = 6,  // per-string scratch (pending-root sums, completion counts)
   kChkDigest = 7,  // digest row
   kChkStack = 8,   // incremental stack slot
+  kChkIncBuf = 9,  // incremental chunk buffer (the buffered bytes, the remainder carried over)
 };
 
 #ifdef HT_CHECK

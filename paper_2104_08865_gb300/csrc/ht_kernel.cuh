@@ -997,9 +997,12 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
         if (!P.inc_fill) {
           base = P.inc_first - item * G;  // completed by a kernel before this one
         } else if constexpr (!ALIGNED) {
-          inc_chunk0_root<W>(P, P.inc_first, P.inc_fill, reinterpret_cast<const uint8_t *>(P.inc_stage_src), ln,
-                             v0, v1);
-          full = true;
+          // (the buffer holds fewer bytes than a chunk; else nothing of the
+          // chunk is read, and nothing climbs)
+          full = HT_IN_RANGE(P, kChkIncBuf, P.inc_fill, G);
+          if (full)
+            inc_chunk0_root<W>(P, P.inc_first, P.inc_fill, reinterpret_cast<const uint8_t *>(P.inc_stage_src),
+                               ln, v0, v1);
           done = true;
         }
       }
@@ -1018,7 +1021,8 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
   if constexpr (INC) {
     if (gw == cw) seed_frontier<W>(P, sp, ln);
     // the bytes after the last whole chunk, for the next update
-    copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, 32 * gw + ln, 32ull * P.total_warps);
+    if (HT_IN_RANGE(P, kChkIncBuf, P.inc_rem_len, G))
+      copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, 32 * gw + ln, 32ull * P.total_warps);
   }
 }
 

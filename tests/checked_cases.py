@@ -95,11 +95,16 @@ for b in (8, 4):
 for width in (16, 40):
     h, ref = pair(width, 8)
     xb = oracle.params(width)["exec_bytes"]
-    n = 600 * 64 * xb + 13 * xb + 101
+    # (a piece above 96 MiB takes the warp-chunk update kernel; width 40's
+    # updates overlap one another)
+    big = (97 << 20) + 5
+    n = 600 * 64 * xb + big + 13 * xb + 101
     data = inputs.stream_bytes_torch(32, 0, n, dev)
     want = oracle.hash_bytes(width, ref, data.cpu().numpy())
+    if width == 40:
+        abi.ht_ctx_set_flags(h.ctx, abi.HT_FLAG_OVERLAP_LAUNCHES)
     inc = abi.ht_inc_create(h.ctx)
-    cuts = [0, 5, 64 * xb + 3, 300 * 64 * xb + 17, n]
+    cuts = [0, 5, 64 * xb + 3, 300 * 64 * xb + 17, 300 * 64 * xb + 17 + big, n]
     for a, c in zip(cuts[:-1], cuts[1:]):
         abi.ht_inc_update(inc, data.data_ptr() + a, c - a)
     got = torch.empty(h.k, dtype=torch.int64, device=dev)
