@@ -470,7 +470,7 @@ int ht_hash_noalloc(int width_bytes, const uint64_t *seed_words_host,
                     uint64_t *digest_dev, ht_stream_t stream);
 
 /* ---- launch shapes and autotuning ------------------------------------------
- * Three kernel families compute the same digests:
+ * Four kernel families compute the same digests:
  *   kernel 0, the stream kernel: every warp owns a ring of `stages`
  *     shared-memory slots, each filled with one bulk copy (TMA) of 8
  *     executions, and hashes an equal, contiguous share of the work;
