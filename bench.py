@@ -12,7 +12,7 @@ the four hashes (4 GiB hashed).  The input is larger than L2 (1 GiB vs
           are inside the timed region.
   roofline  the dominant kernel (the slowest width) against the measured HBM
           copy bandwidth; algorithmic bytes = 2^30 read per launch.
-  cpu_baseline  the CPU oracle on the machine's host cores: all cores at once
+  cpu_baseline  the CPU oracle on the host's cores: all cores at once
           (independent 64 MiB pieces of the string), one thread, and the
           whole string at every width (its digests checked against the GPU's).
   blocks_256  the same string and widths with 256-bit blocks (b = 4 words).
