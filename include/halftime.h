@@ -535,7 +535,8 @@ uint64_t ht_ctx_launches(ht_ctx *ctx);
  * that fit the free device memory (the budget) and a free stream slot,
  * stages pinned-host requests the GPU cannot read in place into a device
  * arena, and launches the batch on that slot's stream -- the batch graph,
- * or one single-string launch for a batch of one request -- with the
+ * or one single-string launch per request for a batch of at most eight
+ * requests -- with the
  * batch's descriptors and digests in pinned host memory the GPU reads and
  * writes in place (else copied there and back); a completion thread
  * retires batches as their events fire, releases their memory and wakes

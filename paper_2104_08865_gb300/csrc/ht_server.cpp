@@ -150,6 +150,16 @@ struct ht_server {
 
 namespace {
 
+// Batches of at most this many requests run as single-string launches, one
+// per request, instead of the batch graph (four planner launches and the
+// batch kernels).  Measured on GB300 (width 32, C5 request mix, eight
+// batches in flight, p50 at 10 / 30 / 50 / 70 / 90 % load): all batches
+// through the graph but lone requests 41-53 / 112 / 154-163 / 263-269 /
+// 653-703 us; up to 4 singles 34 / 78 / 121 / 259-281 / 652-788; up to 8
+// singles 35 / 90 / 113 / 186-195 / 512-533 (p99 at 90 %: 0.96-1.16 ms
+// against 1.21-1.38); up to 16 or 32 singles slower again from 30 % load.
+constexpr size_t kSingleLaunches = 8;
+
 // Enqueues a formed batch: staging copies of pinned requests that the GPU
 // cannot read in place, then one single-string launch (a lone request) or the
 // batch graph, with descriptor and digest copies only where the GPU cannot
@@ -171,14 +181,17 @@ int launch_real(ht_server *S, Slot &sl, const std::vector<Req *> &batch) {
     sl.h_lens[i] = r->len;
   }
   cudaError_t e = cudaSuccess;
-  if (n == 1) {
-    // a lone request (common at low load): one single-string launch instead
-    // of the batch graph's planner and batch kernels (about 25 us less)
+  if (n <= kSingleLaunches) {
+    // a few requests (common at low load): one single-string launch each
+    // instead of the batch graph's planner and batch kernels
     uint64_t *dig = sl.m_digests ? sl.m_digests : sl.d_digests;
-    int rc = ht_hash(sl.ctx, sl.h_ptrs[0], sl.h_lens[0], dig, sl.stream);
-    if (rc) return rc;
+    for (size_t i = 0; i < n; ++i) {
+      int rc = ht_hash(sl.ctx, sl.h_ptrs[i], sl.h_lens[i], dig + i * S->k, sl.stream);
+      if (rc) return rc;
+    }
     if (!sl.m_digests)
-      e = cudaMemcpyAsync(sl.h_digests, sl.d_digests, S->k * sizeof(uint64_t), cudaMemcpyDeviceToHost, sl.stream);
+      e = cudaMemcpyAsync(sl.h_digests, sl.d_digests, n * S->k * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                          sl.stream);
   } else if (sl.m_ptrs) {
     // descriptors read and digests written in place: the batch graph is the
     // only work of the batch (the stores above precede the launch)
