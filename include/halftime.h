@@ -210,9 +210,9 @@ int ht_hash_host(ht_ctx *ctx, const void *data_host, uint64_t len,
 /* Hashes `count` device-resident strings in one persistent launch (the batch
  * form): ptrs_dev[i] / lens_dev[i] (device arrays) describe string i, and
  * digests_dev receives count*k words, string i at digests_dev + i*k.  A
- * device planner (launches over tiles of 1024 strings, then one that maps
- * every work item to its string) turns the lengths into a (string, chunk)
- * work list; warps take chunks from an
+ * device planner (one block for up to 1024 strings; else launches over
+ * tiles of 1024 strings, then, from 16,384 strings, one that maps every work
+ * item to its string) turns the lengths into a (string, chunk) work list; warps take chunks from an
  * atomic cursor; per-string completion counters finish each string's trees
  * and run its finaliser inside the same kernel (a string shorter than one
  * chunk is finished by the warp that hashes it).  The planner and the

@@ -219,7 +219,7 @@ static int ensure_groups(ht_ctx *c, uint64_t groups_needed, cudaStream_t s) {
   HT_CUDA(cudaDeviceSynchronize());
   const uint64_t strings = c->cap_strings;
   free_scratch(c);
-  c->graph_valid = false;
+  for (auto &g : c->graphs) g.valid = false;
   return alloc_scratch(c, groups_needed + groups_needed / 4, strings);
 }
 
@@ -561,8 +561,10 @@ int ht_ctx_create(int width, const uint64_t *seed_words, size_t n_words, ht_stre
 int ht_ctx_destroy(ht_ctx *c) {
   if (!c) return HT_OK;
   cudaDeviceSynchronize();
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-  if (c->graph) cudaGraphDestroy(c->graph);
+  for (auto &g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
   free_scratch(c);
   cudaFree(c->d_seeds);
   cudaFree(c->ctl);
@@ -594,7 +596,7 @@ int ht_ctx_reserve(ht_ctx *c, uint64_t max_total_bytes, size_t max_strings) {
   if (!c || max_strings == 0) return set_error(HT_ERR_ARG, "ht_ctx_reserve: bad arguments");
   HT_CUDA(cudaDeviceSynchronize());
   free_scratch(c);
-  c->graph_valid = false;
+  for (auto &g : c->graphs) g.valid = false;
   return alloc_scratch(c, groups_bound(max_total_bytes / (uint64_t)c->ks->exec_bytes), max_strings);
 }
 
@@ -707,9 +709,13 @@ int ht_hash_host(ht_ctx *c, const void *data, uint64_t len, uint64_t *digest_hos
 
 // The batch graph: planner nodes -> hash node(s).  The warp-chunk and
 // stream kernels take the multi-block planner (tiles -> totals -> write, one
-// thread per string); the hybrid kernel takes the one-block planner, which
-// also lays out its two-phase work list.  Node parameters are replaced on
-// every call; the graph is rebuilt when the batch shape changes.
+// thread per string) for batches of more than 1024 strings, and the
+// one-block planner (one launch instead of three) for smaller ones; the
+// hybrid kernel always takes the one-block planner, which also lays out its
+// two-phase work list.  Each size class has a graph of its own, so that
+// small and large batches alternating (a server) rebuild nothing.  Node
+// parameters are replaced on every call; a graph is rebuilt when the batch
+// shape changes.
 struct BatchNodes {
   cudaKernelNodeParams plan, totals, write, items, hash, hash2;
   void *pargs[1], *hargs[1];
@@ -740,10 +746,18 @@ static bool use_map(const ht_ctx *c, const ht_shape &shape, size_t count) {
          c->ks->batch_map[shape.chunk_levels - 1] != nullptr;
 }
 
-static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
+// Batches of at most this many strings take the one-block planner (512-bit
+// blocks and the paper's tree: its kernels lay out those plans only).
+constexpr size_t kSmallBatch = 1024;
+
+static bool small_batch(const ht_ctx *c, size_t count) {
+  return count <= kSmallBatch && c->ks->lanes == kLanes && !c->ks->tree;
+}
+
+static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n, bool small) {
   const KernelSet &ks = *c->ks;
   const int pl = shape.kernel == 1 ? shape.chunk_levels : 0;
-  n.multi = shape.kernel != 2;
+  n.multi = shape.kernel != 2 && !small;
   n.general = shape.kernel != 0;
   n.map = use_map(c, shape, c->plan_args.count);
   c->plan_args.item_str = n.map ? c->item_str : nullptr;
@@ -797,37 +811,36 @@ static void batch_nodes(ht_ctx *c, const ht_shape &shape, BatchNodes &n) {
   if (n.general) n.hash2.func = (void *)general_batch_kernel(c, shape, n.map);
 }
 
-static int build_batch_graph(ht_ctx *c, const ht_shape &shape) {
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-  if (c->graph) cudaGraphDestroy(c->graph);
-  c->graph_exec = nullptr;
-  c->graph = nullptr;
-  c->node_hash2 = c->node_totals = c->node_write = c->node_items = nullptr;
+static int build_batch_graph(ht_ctx *c, const ht_shape &shape, bool small) {
+  ht_ctx::BatchGraph &g = c->graphs[small ? 0 : 1];
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  g = ht_ctx::BatchGraph();
   BatchNodes n;
-  batch_nodes(c, shape, n);
-  HT_CUDA(cudaGraphCreate(&c->graph, 0));
-  HT_CUDA(cudaGraphAddKernelNode(&c->node_plan, c->graph, nullptr, 0, &n.plan));
-  cudaGraphNode_t last = c->node_plan;
+  batch_nodes(c, shape, n, small);
+  HT_CUDA(cudaGraphCreate(&g.graph, 0));
+  HT_CUDA(cudaGraphAddKernelNode(&g.node_plan, g.graph, nullptr, 0, &n.plan));
+  cudaGraphNode_t last = g.node_plan;
   if (n.multi) {
-    HT_CUDA(cudaGraphAddKernelNode(&c->node_totals, c->graph, &last, 1, &n.totals));
-    last = c->node_totals;
-    HT_CUDA(cudaGraphAddKernelNode(&c->node_write, c->graph, &last, 1, &n.write));
-    last = c->node_write;
+    HT_CUDA(cudaGraphAddKernelNode(&g.node_totals, g.graph, &last, 1, &n.totals));
+    last = g.node_totals;
+    HT_CUDA(cudaGraphAddKernelNode(&g.node_write, g.graph, &last, 1, &n.write));
+    last = g.node_write;
     if (n.map) {
-      HT_CUDA(cudaGraphAddKernelNode(&c->node_items, c->graph, &last, 1, &n.items));
-      last = c->node_items;
+      HT_CUDA(cudaGraphAddKernelNode(&g.node_items, g.graph, &last, 1, &n.items));
+      last = g.node_items;
     }
   }
-  HT_CUDA(cudaGraphAddKernelNode(&c->node_hash, c->graph, &last, 1, &n.hash));
+  HT_CUDA(cudaGraphAddKernelNode(&g.node_hash, g.graph, &last, 1, &n.hash));
   if (n.general) {
     // the general variant; the one the planner's flag does not select
     // returns at once
-    HT_CUDA(cudaGraphAddKernelNode(&c->node_hash2, c->graph, &c->node_hash, 1, &n.hash2));
+    HT_CUDA(cudaGraphAddKernelNode(&g.node_hash2, g.graph, &g.node_hash, 1, &n.hash2));
   }
-  HT_CUDA(cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
-  c->graph_shape = shape;
-  c->graph_map = n.map;
-  c->graph_valid = true;
+  HT_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+  g.shape = shape;
+  g.map = n.map;
+  g.valid = true;
   return HT_OK;
 }
 
@@ -862,22 +875,23 @@ int ht_hash_batch(ht_ctx *c, const void *const *ptrs, const uint64_t *lens, size
   P.unitb0s = c->unitb0s;
   P.digests = (unsigned long long *)digests;
   P.count = (unsigned)count;
-  if (!c->graph_valid || memcmp(&c->graph_shape, &shape, sizeof shape) != 0 ||
-      c->graph_map != use_map(c, shape, count)) {
-    int rc = build_batch_graph(c, shape);
+  const bool small = small_batch(c, count);
+  ht_ctx::BatchGraph &g = c->graphs[small ? 0 : 1];
+  if (!g.valid || memcmp(&g.shape, &shape, sizeof shape) != 0 || g.map != use_map(c, shape, count)) {
+    int rc = build_batch_graph(c, shape, small);
     if (rc) return rc;
   } else {
     BatchNodes n;
-    batch_nodes(c, shape, n);
-    HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_plan, &n.plan));
-    if (c->node_totals) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_totals, &n.totals));
-    if (c->node_write) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_write, &n.write));
-    if (c->node_items) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_items, &n.items));
-    HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash, &n.hash));
-    if (c->node_hash2) HT_CUDA(cudaGraphExecKernelNodeSetParams(c->graph_exec, c->node_hash2, &n.hash2));
+    batch_nodes(c, shape, n, small);
+    HT_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.node_plan, &n.plan));
+    if (g.node_totals) HT_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.node_totals, &n.totals));
+    if (g.node_write) HT_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.node_write, &n.write));
+    if (g.node_items) HT_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.node_items, &n.items));
+    HT_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.node_hash, &n.hash));
+    if (g.node_hash2) HT_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.node_hash2, &n.hash2));
   }
-  HT_CUDA(cudaGraphLaunch(c->graph_exec, s));
-  c->launches.fetch_add(2 + (c->node_totals ? 2 : 0) + (c->node_items ? 1 : 0) + (c->node_hash2 ? 1 : 0));
+  HT_CUDA(cudaGraphLaunch(g.exec, s));
+  c->launches.fetch_add(2 + (g.node_totals ? 2 : 0) + (g.node_items ? 1 : 0) + (g.node_hash2 ? 1 : 0));
   return HT_OK;
 }
 

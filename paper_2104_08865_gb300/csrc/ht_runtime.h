@@ -40,15 +40,18 @@ struct ht_ctx {
   uint64_t cap_groups = 0, cap_strings = 0;
   // launch shapes: [0..63] by floor(log2(len)), [64] batches
   ht_shape shapes[65];
-  // batch graph: planner -> persistent kernel
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
-  cudaGraphNode_t node_plan = nullptr, node_hash = nullptr, node_hash2 = nullptr;
-  cudaGraphNode_t node_totals = nullptr, node_write = nullptr;  // multi-block planner (else null)
-  cudaGraphNode_t node_items = nullptr;  // item -> string map (warp-chunk kernel, L >= 2; else null)
-  ht_shape graph_shape = {};
-  bool graph_map = false;  // the graph's planner writes the item map and its kernels read it
-  bool graph_valid = false;
+  // batch graphs (planner -> persistent kernel): [0] for batches of up to
+  // 1024 strings, planned by one block, [1] for the others
+  struct BatchGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t node_plan = nullptr, node_hash = nullptr, node_hash2 = nullptr;
+    cudaGraphNode_t node_totals = nullptr, node_write = nullptr;  // multi-block planner (else null)
+    cudaGraphNode_t node_items = nullptr;  // item -> string map (warp-chunk kernel, L >= 2; else null)
+    ht_shape shape = {};
+    bool map = false;  // the planner writes the item map and the kernels read it
+    bool valid = false;
+  } graphs[2];
   ht::PlanArgs plan_args = {};
   ht::KParams batch_params = {};
   // host-input pipeline

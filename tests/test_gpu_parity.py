@@ -233,20 +233,20 @@ def test_launch_counter_counts_kernels(dev):
     torch.cuda.synchronize()
     from paper_2104_08865_gb300 import abi
     batch_kernel = abi.ht_get_shape(h.ctx, 2**64 - 1)["kernel"]
-    # one hash kernel, then the planner (three launches, one for the hybrid
-    # family) and the batch kernels (an aligned and a general one, except for
-    # the stream family)
-    assert h.launches() - before == 1 + {0: 4, 1: 5, 2: 3}[batch_kernel]
+    # one hash kernel, then the planner (one launch for batches of up to
+    # 1024 strings) and the batch kernels (an aligned and a general one,
+    # except for the stream family)
+    assert h.launches() - before == 1 + {0: 2, 1: 3, 2: 3}[batch_kernel]
     if batch_kernel == 1:
-        # a batch of 16,384 strings or more: a fourth planner launch writes
-        # the item -> string map
-        n = 20_000
-        ptrs = torch.full((n,), dbuf.data_ptr(), dtype=torch.int64, device=dev)
-        ln = torch.full((n,), 100, dtype=torch.int64, device=dev)
-        before = h.launches()
-        h.hash_batch(ptrs, ln, n)
-        torch.cuda.synchronize()
-        assert h.launches() - before == 6
+        # more than 1024 strings: the multi-block planner (three launches);
+        # 16,384 or more: a fourth planner launch writes the item -> string map
+        for n, launches in ((2_000, 5), (20_000, 6)):
+            ptrs = torch.full((n,), dbuf.data_ptr(), dtype=torch.int64, device=dev)
+            ln = torch.full((n,), 100, dtype=torch.int64, device=dev)
+            before = h.launches()
+            h.hash_batch(ptrs, ln, n)
+            torch.cuda.synchronize()
+            assert h.launches() - before == launches, n
 
 
 def test_python_layer_rejects_bad_tensors(dev):
