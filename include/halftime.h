@@ -310,7 +310,10 @@ int ht_finish_parts(ht_ctx *ctx, uint64_t *digest_dev, ht_stream_t stream);
  *     Different handles are independent (each has its own scratch).
  *   - The state can be saved to host memory and restored into another
  *     handle of a context with the same width and seed words, in this or
- *     another process, to resume the string later. */
+ *     another process, to resume the string later.
+ *   - After an update that returns an error the open string is lost (an
+ *     update of more than 65536 chunks may have launched part of its work):
+ *     ht_inc_init starts a new one, ht_inc_import resumes a saved state. */
 
 /* Creates a handle (1.3 to 3.1 MB of device memory by width; host updates add
  * two staging slots of 1024 chunks) with an open, empty string.
