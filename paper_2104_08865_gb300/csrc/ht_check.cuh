@@ -2,10 +2,11 @@
 // -DHT_CHECK into libhalftime_check.so; compute-sanitizer is not available
 // everywhere, so the library can check itself).
 //
-// In a checked build every global-memory access of the warp-chunk kernels
-// is preceded by a check of its index against the extent of its buffer: the
-// input string, a seed region, the tree-group scratch, the per-string
-// scratch, the digests, the incremental stack.  An index outside its buffer
+// In a checked build every global-memory access of the kernels (all four
+// families; a bulk copy by its whole range) is preceded by a check of its
+// index against the extent of its buffer: the input string, a seed region,
+// the tree-group scratch, the per-string scratch, the digests, the
+// incremental stack and chunk buffers.  An index outside its buffer
 // is not accessed: the check records the first such (kind, index) in the
 // launch's control block, sets a status bit, and the access is skipped, so
 // the kernel neither faults nor traps; the host reports it as

@@ -63,6 +63,7 @@ __device__ __forceinline__ void hash_round(const KParams &P, const StrPlan &sp, 
   for (int i = 0; i < m; ++i) {
     uint64_t y[2][k];
     const uint8_t *e1 = ex + i * B;
+    if (kChecked && !HT_IN_RANGE(P, kChkInput, (8 * gx + i + 1) * B - 1, sp.len)) continue;
     if (al)
       ehc2_from<W>([&](int b) { return ld_stream(e1 + b * 64); }, P, y);
     else
@@ -125,7 +126,7 @@ __device__ __forceinline__ void hash_unit(const KParams &P, const StrPlan &sp, u
   const uint32_t sh = (uint32_t)(((uintptr_t)sp.ptr) & 15u);
   const uint8_t *e1 = sp.ptr + (8 * g + (uint64_t)x) * B + p * 16;
   uint64_t y[2][k];
-  if (x < m) {
+  if (x < m && HT_IN_RANGE(P, kChkInput, (8 * g + (uint64_t)x + 1) * B - 1, sp.len)) {
     if (ALIGNED || sh == 0)
       ehc2_from<W>([&](int b) { return ld_stream(e1 + b * 64); }, P, y);
     else

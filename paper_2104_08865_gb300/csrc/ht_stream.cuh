@@ -46,6 +46,12 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
       : "memory");
 }
 
+// One arrival without data (the checked build's stand-in for a skipped
+// copy: the stage's phase still completes).
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // Waits for the phase of `parity` to complete; false after `budget` cycles.
 // The clock is read before every try (a try may itself suspend the thread
 // for a while), so a budget of a few cycles runs out before the first try.
@@ -311,7 +317,10 @@ __global__ void __launch_bounds__(256) stream_kernel(const __grid_constant__ KPa
           const uint64_t m = pc.sp.n_exec - 8 * pc.g < 8 ? pc.sp.n_exec - 8 * pc.g : 8;
           const unsigned sl = (unsigned)(pseq % R);
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          bulk_load(slots + sl * SLOT, pc.sp.ptr + 8 * pc.g * B, (uint32_t)(m * B), bars + 8 * sl);
+          if (HT_IN_RANGE(P, kChkInput, (8 * pc.g + m) * B - 1, pc.sp.len))
+            bulk_load(slots + sl * SLOT, pc.sp.ptr + 8 * pc.g * B, (uint32_t)(m * B), bars + 8 * sl);
+          else
+            mbar_arrive(bars + 8 * sl);
           ++pseq;
         }
         ++pu;
@@ -337,7 +346,8 @@ __global__ void __launch_bounds__(256) stream_kernel(const __grid_constant__ KPa
       } else {
         const uint8_t *ex = sp.ptr + (8 * g + (uint64_t)x) * B + p * 16;
         const uint32_t sh = (uint32_t)(((uintptr_t)sp.ptr) & 15u);
-        if (x < m) ehc2_from<W>([&](int b) { return ld_unaligned(ex + b * 64, sh); }, P, y);
+        if (x < m && HT_IN_RANGE(P, kChkInput, (8 * g + (uint64_t)x + 1) * B - 1, sp.len))
+          ehc2_from<W>([&](int b) { return ld_unaligned(ex + b * 64, sh); }, P, y);
       }
       if (m == 8) {
         uint64_t n1[2][k];

@@ -72,6 +72,36 @@ for b in (8, 4):
                 assert np.array_equal(got, w2), ("unaligned batch", b, width)
         h.close()
 
+# 2a. every kernel family by its launch shape (stream with TMA stages,
+#     warp-chunk, hybrid, block-chunk): single strings, aligned and at a
+#     3-byte offset, and batches
+for width in (24, 40):
+    h, ref = pair(width, 8)
+    xb = oracle.params(width)["exec_bytes"]
+    lens = [0, 7, 5 * xb + 9, 64 * xb, 520 * xb + 3 * xb + 77, 4096 * xb + 1]
+    buf, offs = inputs.packed_batch(33, [n + 3 for n in lens])
+    dbuf = torch.from_numpy(buf).to(dev)
+    for shape in ((0, 2, 3, 128, 1), (1, 2, 3, 256, 2), (2, 2, 3, 256, 2), (3, 2, 3, 256, 2)):
+        for bucket in range(64):
+            abi.ht_set_shape(h.ctx, 1 << bucket, *shape)
+        if shape[0] != 3:
+            abi.ht_set_shape(h.ctx, 2**64 - 1, *shape)
+        for sh in (0, 3):
+            want = np.stack([oracle.hash_bytes(width, ref, buf[int(o) + sh:int(o) + sh + n])
+                             for o, n in zip(offs, lens)])
+            out = torch.empty((len(lens), h.k), dtype=torch.int64, device=dev)
+            for i, (o, n) in enumerate(zip(offs, lens)):
+                h.hash(dbuf, n, out=out[i], offset=int(o) + sh)
+            h.status()
+            assert np.array_equal(u64(out), want), ("family single", width, shape, sh)
+            if shape[0] != 3:
+                ptrs = torch.tensor([dbuf.data_ptr() + int(o) + sh for o in offs], dtype=torch.int64, device=dev)
+                ln = torch.tensor(lens, dtype=torch.int64, device=dev)
+                got = u64(h.hash_batch(ptrs, ln, len(lens)))
+                h.status()
+                assert np.array_equal(got, want), ("family batch", width, shape, sh)
+    h.close()
+
 # 2b. a batch of 20,000 strings: the planner's item map and the batch kernel
 #     instance that reads it
 for b in (8, 4):
