@@ -165,7 +165,9 @@ __global__ void __launch_bounds__(256, 2) block_kernel(const __grid_constant__ K
   }
   griddep_wait();
   if constexpr (INC) {
-    if (blockIdx.x == nb && w == 0) seed_frontier<W>(P, sp, ln);
+    // (its eight warps take the levels in turn: each level's arrivals and
+    // climbs are independent of the others')
+    if (blockIdx.x == nb) seed_frontier<W>(P, sp, ln, w, 8);
     // the bytes after the last whole chunk, for the next update
     if (HT_IN_RANGE(P, kChkIncBuf, P.inc_rem_len, 64 * XB))
       copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,

@@ -834,7 +834,7 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, u
   if (old == sp.n_items - 1) finish_string<W, B>(P, sp, sidx, ln);
 }
 
-// Incremental update, one warp: the stack carries, for every level, the
+// Incremental update, the frontier: the stack carries, for every level, the
 // nodes of its last, incomplete group (d of them).  If the update completes
 // that group, the d nodes enter it as one arrival of d children (the sum of
 // their tree-key NH terms); arrivals are sums and counts, so the order
@@ -842,14 +842,22 @@ __device__ void hash_chunk(const KParams &P, const StrPlan &sp, unsigned sidx, u
 // count to 8 takes the parent node and climbs on.  Otherwise the d nodes stay
 // pending and are copied to the same positions of the new stack (the
 // update's own pending nodes of that level come after them).  The previous
-// stack is only read, so no other warp's writes can race with this.
+// stack is only read, so no other warp's writes can race with this.  The
+// levels are independent of one another (a node climbing out of one level
+// arrives in the next one's group beside its stack nodes, at a position the
+// copy does not touch), so several warps may split them.
 template <int W>
-__device__ void seed_frontier(const KParams &P, const StrPlan &sp, int ln) {
+__device__ void seed_frontier(const KParams &P, const StrPlan &sp, int ln, int part = 0, int parts = 1) {
   constexpr int k = Spec<W>::k;
   const int x = ln >> 2, p = ln & 3;
   const uint64_t N0 = sp.chunk0 << 6, N1 = sp.n_exec;
   uint64_t goff = 0;
   for (int lvl = 2; lvl < kLevels; ++lvl) {
+    // (levels are independent: warp `part` of `parts` takes every parts-th)
+    if ((lvl - 2) % parts != part) {
+      if (lvl < kLevels - 1) goff = next_goff<true>(sp, lvl, goff);
+      continue;
+    }
     const uint64_t n0 = N0 >> (3 * lvl), n1 = N1 >> (3 * lvl);
     const unsigned d = (unsigned)(n0 & 7);
     const bool completes = (n1 >> 3) > (n0 >> 3);
