@@ -105,11 +105,13 @@ void inc_params(const ht_inc *h, KParams &P) {
 
 // Updates of fewer bytes than this run the block-chunk kernel (a block of
 // eight warps per chunk, one execution per thread; its block for the first
-// chunk reads it with 256 threads).  Measured on GB300 (width 24, pieces
-// back to back with overlapping launches): 64 MiB + 3 bytes 25.6 us per
-// update against 27.1 with the warp-chunk kernel, 128 MiB + 3 bytes 41.4
-// against 33.4.
-constexpr uint64_t kBlockwiseBytes = 96ull << 20;
+// chunk reads it with 256 threads), longer ones the warp-chunk kernel (with
+// eight warps on a first chunk read from two places).  Measured on GB300
+// (width 24, pieces back to back with overlapping launches, us per update):
+// 16 MiB + 3 bytes 11.3 (block) / 11.2 (warp), 32 MiB + 3 15.6 / 15.6,
+// 64 MiB + 3 24.3 / 17.7, 780 whole chunks 22.7 / 15.7, 128 MiB + 3
+// 29.0 / 28.8.
+constexpr uint64_t kBlockwiseBytes = 32ull << 20;
 
 // Hashes chunks [h->chunks, h->chunks + M): the first from the chunk buffer
 // if first_from_buf, the others (or all) contiguous at ptr (device).  One
@@ -125,7 +127,9 @@ int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, c
   ht_ctx *c = h->ctx;
   const KernelSet &ks = *c->ks;
   const uint64_t C = h->chunks;
-  if (groups_for_update(C, M) > h->cap_groups)
+  // (the last slot is the first chunk's level-1 group of warp-chunk updates
+  // that read that chunk from two places)
+  if (groups_for_update(C, M) > h->cap_groups - 1)
     return set_error(HT_ERR_ARG, "incremental update needs more group slots than reserved");
   KParams P;
   inc_params(h, P);
@@ -162,10 +166,12 @@ int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, c
     grid = (M + rounds - 1) / rounds + 1;
   } else {
     // whole rounds of cursor grabs (see the one-shot launch), one round
-    // spread over every SM, and one more warp that seeds the frontier
+    // spread over every SM, and one more warp that seeds the frontier; a
+    // first chunk read from two places goes to eight warps of its own
+    const uint64_t Mc = M - (P.inc_fill ? 1 : 0);  // chunks from the cursor
     const uint64_t wmax = (uint64_t)c->num_sms * bps * wpb;
-    const uint64_t rounds = (M + wmax - 1) / wmax;
-    const uint64_t warps = (M + rounds - 1) / rounds + 1;
+    const uint64_t rounds = std::max<uint64_t>(1, (Mc + wmax - 1) / wmax);
+    const uint64_t warps = (Mc + rounds - 1) / rounds + (P.inc_fill ? 9 : 1);
     grid = std::max<uint64_t>(1, (warps + wpb - 1) / wpb);
     if (rounds == 1 && grid < (uint64_t)c->num_sms) {
       wpb = std::max<uint64_t>(1, warps / (uint64_t)c->num_sms);
@@ -173,8 +179,9 @@ int run_chunks(ht_inc *h, bool first_from_buf, const uint8_t *ptr, uint64_t M, c
     }
   }
   grid = std::max<uint64_t>(grid, 1);
-  P.item_begin = C;
+  P.item_begin = C + (!blockwise && P.inc_fill ? 1 : 0);
   P.item_end = C + M;
+  P.inc_chunk0_slot = h->cap_groups - 1;
   P.total_warps = (unsigned)(grid * wpb);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);

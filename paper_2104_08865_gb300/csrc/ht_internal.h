@@ -75,6 +75,7 @@ struct KParams {
   const uint8_t *inc_first;     // incremental mode: bytes of chunk chunk0 if not at ptr (else null)
   unsigned long long inc_fill;  // block-chunk update: only this many bytes of it are at inc_first
   unsigned long long inc_stage_src;  // ... and the rest start the update, at this address
+  unsigned long long inc_chunk0_slot;  // warp-chunk update with inc_fill: the first chunk's group slot
   // incremental mode: the bytes after the update's last whole chunk, which
   // the kernel copies into the handle's other buffer for the next update
   const uint8_t *inc_rem_src;

@@ -898,62 +898,68 @@ __device__ void seed_frontier(const KParams &P, const StrPlan &sp, int ln, int p
   }
 }
 
-// The level-2 root of an incremental update's first chunk (complete: 64
-// executions) when the handle's buffer holds only its first `fill` bytes
-// and the others start the update at src: thread (x, p) hashes executions
-// 8x .. 8x+7, each read where its bytes are (the buffer, the update at any
-// alignment, or, for the execution across the boundary, a copy the warp
-// makes in shared memory), and the levels are formed as chunk_root does for
-// a full chunk.  Returns the root's lanes 2p, 2p+1 of tree x in v0, v1.
+// One of the eight warps that hash an incremental update's first chunk
+// (complete: 64 executions) when the handle's buffer holds only its first
+// `fill` bytes and the others start the update at src: warp j takes level-1
+// node j, thread x execution 8j + x, read where its bytes are (the buffer,
+// the update at any alignment, or, for the execution across the boundary, a
+// copy the warp makes in shared memory), forms the node by shuffles and adds
+// its NH term in the chunk's level-2 node to group slot `slot` (one arrival);
+// the eighth arrival takes the level-2 node and climbs from there.  Eight
+// warps side by side instead of one warp's eight executions in a row.
 template <int W>
-__device__ __forceinline__ void inc_chunk0_root(const KParams &P, const uint8_t *buf, uint64_t fill,
-                                                const uint8_t *src, int ln, uint64_t &v0, uint64_t &v1) {
+__device__ __forceinline__ void inc_chunk0_part(const KParams &P, const StrPlan &sp, int j, uint64_t slot,
+                                                int ln) {
   constexpr int k = Spec<W>::k;
   constexpr uint64_t XB = Dims<W>::exec_bytes;
   __shared__ __align__(16) uint4 across[XB / 16];  // (one warp per block uses it)
   const int x = ln >> 2, p = ln & 3;
-  const uint64_t ea = fill / XB;
-  if (fill % XB)
+  const uint8_t *buf = P.inc_first;
+  const uint64_t fill = P.inc_fill;
+  const uint8_t *src = reinterpret_cast<const uint8_t *>(P.inc_stage_src);
+  const uint64_t ea = fill / XB;  // the execution across the boundary (if fill % XB)
+  if (fill % XB && (uint64_t)j == ea / 8)
     for (uint32_t g = (uint32_t)ln; g < XB / 16; g += 32) across[g] = chunk_granule(buf, src, fill, ea * XB + 16ull * g);
   __syncwarp();
-  uint64_t n1[2][k];
-#pragma unroll
-  for (int l = 0; l < 2; ++l)
-#pragma unroll
-    for (int t = 0; t < k; ++t) n1[l][t] = 0;
-#pragma unroll 1
-  for (int s = 0; s < 8; ++s) {
-    const uint64_t e = 8ull * x + s;
-    const uint8_t *ex;
-    uint32_t esh = 0;
-    bool generic = false;
-    if ((e + 1) * XB <= fill) {
-      ex = buf + e * XB;
-    } else if (e * XB >= fill) {
-      ex = src + (e * XB - fill);
-      esh = (uint32_t)((uintptr_t)ex & 15u);
-    } else {
-      ex = reinterpret_cast<const uint8_t *>(across);
-      generic = true;
-    }
-    uint64_t y[2][k];
-    ehc2<W, false>(ex, p, esh, P, y, generic);
-#pragma unroll
-    for (int l = 0; l < 2; ++l)
-#pragma unroll
-      for (int t = 0; t < k; ++t) n1[l][t] += (s < 7) ? nh64(y[l][t], P.T0[t][s]) : y[l][t];
+  const uint64_t e = 8ull * j + x;
+  const uint8_t *ex;
+  uint32_t esh = 0;
+  bool generic = false;
+  if ((e + 1) * XB <= fill) {
+    ex = buf + e * XB;
+  } else if (e * XB >= fill) {
+    ex = src + (e * XB - fill);
+    esh = (uint32_t)((uintptr_t)ex & 15u);
+  } else {
+    ex = reinterpret_cast<const uint8_t *>(across);
+    generic = true;
   }
-  v0 = 0;
-  v1 = 0;
+  uint64_t y[2][k];
+  ehc2<W, false>(ex, p, esh, P, y, generic);
+  uint64_t a0 = 0, a1 = 0;
 #pragma unroll
   for (int t = 0; t < k; ++t) {
-    const uint64_t key = x < 7 ? tree_key<W>(P, t, 1, x) : 0;
-    const uint64_t a0 = x_sum(x < 7 ? nh64(n1[0][t], key) : n1[0][t]);
-    const uint64_t a1 = x_sum(x < 7 ? nh64(n1[1][t], key) : n1[1][t]);
+    const uint64_t key = x < 7 ? tree_key<W>(P, t, 0, x) : 0;
+    const uint64_t n0 = x_sum(x < 7 ? nh64(y[0][t], key) : y[0][t]);
+    const uint64_t n1 = x_sum(x < 7 ? nh64(y[1][t], key) : y[1][t]);
     if (x == t) {
-      v0 = a0;
-      v1 = a1;
+      // node j's term in the level-2 node (the eighth child enters unhashed)
+      const uint64_t key2 = j < 7 ? tree_key<W>(P, t, 1, j) : 0;
+      a0 = j < 7 ? nh64(n0, key2) : n0;
+      a1 = j < 7 ? nh64(n1, key2) : n1;
     }
+  }
+  if (x < k && HT_IN_RANGE(P, kChkGroup, slot, P.scr.cap_groups)) {
+    unsigned long long *acc = P.scr.grp_acc + (slot * k + (uint64_t)x) * kLanes + 2 * p;
+    atomicAdd(acc, (unsigned long long)a0);
+    atomicAdd(acc + 1, (unsigned long long)a1);
+  }
+  if (arrive(P, slot, ln, 1) == kFan) {
+    uint64_t pend[k];  // (unused: incremental pending nodes go to the stack)
+    bool anyp = false;
+    uint64_t v0 = 0, v1 = 0;
+    take_group<W>(P, slot, ln, v0, v1);
+    climb<W, true>(P, sp, 2, sp.chunk0, 0, v0, v1, ln, pend, anyp);
   }
 }
 
@@ -970,16 +976,19 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
   constexpr int k = Spec<W>::k;
   constexpr uint64_t G = (1ull << (3 * L)) * Dims<W>::exec_bytes;
   const StrPlan &sp = P.single;
-  // warps that take chunks (an incremental update's last warp seeds the
-  // frontier instead, beside them)
-  const uint64_t cw = INC ? P.total_warps - 1 : P.total_warps;
+  // warps that take chunks: in an incremental update the last warp seeds the
+  // frontier instead, beside them, and, when the buffer holds only part of
+  // the update's first chunk, the eight warps before it hash that chunk
+  // (the others start at the chunk after it)
+  const uint64_t extra = INC ? (P.inc_fill ? 9 : 1) : 0;
+  const uint64_t cw = P.total_warps - extra;
   bool first = true;
   for (;;) {
     unsigned long long item = 0;
     if (first) {
       // each warp's first chunk is fixed, so it can be hashed before an
       // overlapping launch's predecessor has finished with the scratch
-      if (INC && gw == cw) break;
+      if (INC && gw >= cw) break;
       item = P.item_begin + gw;
       first = false;
     } else {
@@ -995,27 +1004,15 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
     bool anyp = false;
     uint64_t v0, v1;
     const uint8_t *base = sp.ptr;
-    bool full;
-    bool done = false;  // the root is formed (the update's first chunk, read from two places)
     if constexpr (INC) {
       if (P.inc_first && item == sp.chunk0) {
-        // the update's first chunk: its first bytes were left in the
-        // handle's buffer by the kernel before this one
+        // the update's first chunk, completed in the handle's buffer by the
+        // kernel before this one
         griddep_wait();
-        if (!P.inc_fill) {
-          base = P.inc_first - item * G;  // completed by a kernel before this one
-        } else if constexpr (!ALIGNED) {
-          // (the buffer holds fewer bytes than a chunk; else nothing of the
-          // chunk is read, and nothing climbs)
-          full = HT_IN_RANGE(P, kChkIncBuf, P.inc_fill, G);
-          if (full)
-            inc_chunk0_root<W>(P, P.inc_first, P.inc_fill, reinterpret_cast<const uint8_t *>(P.inc_stage_src),
-                               ln, v0, v1);
-          done = true;
-        }
+        base = P.inc_first - item * G;
       }
     }
-    if (!done) full = chunk_root<W, L, ALIGNED, B>(P, sp, base, item, ln, pend, anyp, v0, v1);
+    const bool full = chunk_root<W, L, ALIGNED, B>(P, sp, base, item, ln, pend, anyp, v0, v1);
     // everything below touches the scratch: an overlapping launch must first
     // see its predecessor finish
     griddep_wait();
@@ -1027,7 +1024,13 @@ __device__ __forceinline__ void single_string(const KParams &P, uint64_t gw, int
   }
   griddep_wait();
   if constexpr (INC) {
-    if (gw == cw) seed_frontier<W>(P, sp, ln);
+    if (gw == P.total_warps - 1) seed_frontier<W>(P, sp, ln);
+    if constexpr (!ALIGNED) {
+      // (the buffer holds fewer bytes than a chunk; else nothing of the
+      // chunk is read)
+      if (P.inc_fill && gw >= cw && gw < cw + 8 && HT_IN_RANGE(P, kChkIncBuf, P.inc_fill, G))
+        inc_chunk0_part<W>(P, sp, (int)(gw - cw), P.inc_chunk0_slot, ln);
+    }
     // the bytes after the last whole chunk, for the next update
     if (HT_IN_RANGE(P, kChkIncBuf, P.inc_rem_len, G))
       copy_bytes(P.inc_rem_dst, P.inc_rem_src, P.inc_rem_len, 32 * gw + ln, 32ull * P.total_warps);

@@ -125,7 +125,7 @@ for b in (8, 4):
 for width in (16, 40):
     h, ref = pair(width, 8)
     xb = oracle.params(width)["exec_bytes"]
-    # (a piece above 96 MiB takes the warp-chunk update kernel; width 40's
+    # (a piece above 32 MiB takes the warp-chunk update kernel; width 40's
     # updates overlap one another)
     big = (97 << 20) + 5
     n = 600 * 64 * xb + big + 13 * xb + 101
