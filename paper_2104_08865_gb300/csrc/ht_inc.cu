@@ -4,8 +4,8 @@
 // The handle holds the string's eager tree counter between calls (Section
 // 5.2: the pending nodes of every level, kept on a stack) and a buffer for
 // bytes that do not yet fill a 64-execution chunk.  Updates run the
-// warp-chunk kernel in its incremental mode over whole chunks, straight from
-// the caller's memory; only the bytes after an update's last whole chunk
+// block-chunk kernel (below 32 MiB) or the warp-chunk kernel in its
+// incremental mode over whole chunks, straight from the caller's memory; only the bytes after an update's last whole chunk
 // are copied (by the update kernel itself, into the handle's other buffer),
 // and the next update reads its first chunk from the buffer and from its
 // own first bytes, so that an update is one kernel that may overlap the one

@@ -2,8 +2,9 @@
 //
 // An update hashes whole 64-execution chunks, the level-2 nodes of the
 // string's trees (Section 5.2), in the string's global chunk frame, with the
-// warp-chunk kernel in its incremental mode (its first warp also starts the
-// groups that the update completes from the stack: seed_frontier).  Between
+// block-chunk or the warp-chunk kernel in its incremental mode (a block or a
+// warp of its own also starts the groups that the update completes from the
+// stack: seed_frontier).  Between
 // updates the trees' eager counter is carried on a stack: for every level
 // l >= 2 the nodes of the last, incomplete group, which are the pending nodes
 // of a string that ends here, one value per tree and lane.  When the string
